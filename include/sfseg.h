@@ -1,0 +1,180 @@
+/*
+ * sfseg.h -- C-ABI of the GB300 (sm_103a) SFSeg power-iteration library.
+ *
+ * SFSeg ("A 3D Convolutional Approach to Spectral Object Segmentation in
+ * Space and Time", Burceanu & Leordeanu) segments a video by the principal
+ * eigenvector of the pixel-level space-time adjacency matrix
+ *
+ *     M_ij = sp_i sp_j [1 - alpha (f_i - f_j)^2] G_ij,   sp = S^p     (Eq. 2)
+ *
+ * where G is a Gaussian over the space-time offset of voxels i and j,
+ * truncated to a box of radii (rt, ry, rx).  M is never formed: one power
+ * step x <- M x / ||M x|| (Eq. 4, Eq. 8) is evaluated as point-wise products
+ * and three separable 3D Gaussian convolutions of the feature volume (Eq. 7).
+ *
+ * Conventions shared by every entry point
+ *   - Volumes are dense, C-contiguous FP32 arrays [nf][h][w] (w fastest) in
+ *     DEVICE memory, owned by the caller and only borrowed for the call.
+ *   - All work is queued on the caller's CUDA stream (`stream` is a
+ *     cudaStream_t; NULL = legacy default stream) and is asynchronous unless
+ *     the function says it synchronises.
+ *   - Every function returns an sfseg_status; nothing aborts or traps.
+ *     sfseg_last_error() gives a message for the last failure on a context.
+ *   - A context is not thread-safe: use one context per stream/thread.
+ *   - The volume border is zero padding (neighbours outside the volume do
+ *     not exist), which keeps M symmetric.  G is the per-axis Gaussian
+ *     g(d) = exp(-d^2 / 2 sigma^2) with peak 1, not renormalised.  The
+ *     neighbourhood of a voxel contains the voxel itself.
+ *   - The operator applied is exactly M of Eq. 2 (Eq. 7 of the paper omits
+ *     the overall factor alpha of Eq. 6; eigenvectors are unaffected), so the
+ *     Rayleigh quotients reported are eigenvalue estimates of M.
+ */
+#ifndef SFSEG_H
+#define SFSEG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfseg_ctx sfseg_ctx;   /* opaque; owns all device workspace */
+
+typedef enum {
+    SFSEG_OK = 0,
+    SFSEG_EINVAL = 1,        /* invalid argument (message in sfseg_last_error) */
+    SFSEG_ENOMEM = 2,        /* device or host allocation failed */
+    SFSEG_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SFSEG_EZERONORM = 4,     /* ||M x|| = 0 at some step (x0 orthogonal to the support) */
+    SFSEG_ENONFINITE = 5,    /* NaN/Inf in the inputs or in a norm */
+    SFSEG_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    SFSEG_EUNSUPPORTED = 7,  /* valid request this build does not implement */
+    SFSEG_ESTATE = 8         /* call order (e.g. adjoint without a recorded forward) */
+} sfseg_status;
+
+typedef enum {
+    SFSEG_F32 = 0,           /* FP32 storage of sp, f and the iterate */
+    SFSEG_BF16 = 1,          /* BF16 storage, FP32 arithmetic, FP64 reductions */
+    SFSEG_F16 = 2            /* FP16 storage (iterate stored scaled to RMS ~ 1) */
+} sfseg_dtype;
+
+/* sfseg_params.flags */
+enum {
+    SFSEG_S_IS_SP = 1,       /* d_s already holds S^p; p is ignored */
+    SFSEG_NO_GRAPH = 2,      /* launch the iteration loop eagerly (no CUDA graph) */
+    SFSEG_RECORD = 4,        /* record checkpoints during power_iterate for sfseg_adjoint */
+    SFSEG_GENERIC = 8        /* force the generic (any-radius) stencil kernel */
+};
+
+typedef struct {
+    int32_t nf, h, w;        /* volume: frames x rows x cols, all >= 1 */
+    int32_t rt, ry, rx;      /* Gaussian radii (extent 2r+1), 0 <= r <= 16 */
+    double sigma_t, sigma_y, sigma_x;  /* Gaussian widths, > 0 */
+    double alpha;            /* weight of the pairwise feature term, >= 0 */
+    double p;                /* unary exponent: sp = S^p, >= 0 */
+    int32_t storage;         /* sfseg_dtype */
+    int32_t flags;           /* SFSEG_* flags above */
+    int32_t nchan;           /* pairwise feature channels C >= 1 (Eq. 9); d_f is [C][nf][h][w] */
+    int32_t ckpt_every;      /* adjoint checkpoint interval in steps (0 = 8) */
+} sfseg_params;
+
+/* Fill `prm` with defaults for an nf x h x w volume: radii (2, 5, 5),
+ * sigma_t = 1.5, sigma_xy = 3, alpha = 1, p = 0.1 (the paper's unsupervised
+ * setting, Sec. 5), FP32 storage, one channel. */
+void sfseg_default_params(sfseg_params* prm, int32_t nf, int32_t h, int32_t w);
+
+/* Create a context for one volume shape (Sec. 3 defines the operator; the
+ * context allocates the device workspace: internal pitched copies of sp, f,
+ * the two iterate buffers, reduction partials and the trace).
+ * Errors: EINVAL (bad params), ENOMEM, ECUDA.  *out is NULL on failure. */
+sfseg_status sfseg_create(const sfseg_params* prm, sfseg_ctx** out);
+
+/* Create one context for a batch of independent videos of uneven shape that
+ * share radii/sigmas/alpha/p/storage (`prm`'s nf/h/w are ignored).
+ * dims: host array [n_videos][3] of (nf, h, w).  One persistent launch per
+ * power step covers every video; each video keeps its own norm, Rayleigh
+ * quotient and trace. */
+sfseg_status sfseg_create_batched(const sfseg_params* prm, int32_t n_videos,
+                                  const int32_t* dims, sfseg_ctx** out);
+
+void sfseg_destroy(sfseg_ctx* ctx);   /* NULL is a no-op; synchronises the device */
+
+/* Load the features into the context: sp = S^p (Eq. 1's unary term; S is
+ * taken as-is with SFSEG_S_IS_SP) and f, converted to the storage type.
+ * d_s: [nf][h][w] FP32; d_f: [nchan][nf][h][w] FP32 (device).  For a batched
+ * context use sfseg_load_features_batched.  Errors: EINVAL, ECUDA. */
+sfseg_status sfseg_load_features(sfseg_ctx* ctx, const float* d_s, const float* d_f,
+                                 void* stream);
+
+/* Power iteration (Eq. 4 + Eq. 8, Algorithm 1 without binarisation).
+ *   d_s, d_f : features as in sfseg_load_features, or both NULL to reuse the
+ *              features loaded last;
+ *   d_x      : in: x0 (any scale, not all zero); out: x^K, unit L2 norm, FP32;
+ *   n_iters  : K >= 0 power steps;
+ *   tol      : 0 = exactly K steps; > 0 = stop after the first step k with
+ *              rho_k / r_k < tol (r_k Rayleigh quotient, rho_k residual);
+ *   iters_done: nullable host pointer; if given, the call synchronises the
+ *              stream and stores the number of steps taken.
+ * Step k computes y = M x^k, r_k = x^k.y / x^k.x^k, rho_k = ||y - r_k x^k|| /
+ * ||x^k||, x^{k+1} = y / ||y||; r_k, rho_k and ||y|| go to the device trace.
+ * Errors (reported by this call, or by the next synchronising call when the
+ * device detects them): EINVAL, ECUDA, EZERONORM, ENONFINITE. */
+sfseg_status sfseg_power_iterate(sfseg_ctx* ctx, const float* d_s, const float* d_f,
+                                 float* d_x, int32_t n_iters, double tol,
+                                 int32_t* iters_done, void* stream);
+
+/* Batched form: host arrays of n_videos device pointers (x in/out per video). */
+sfseg_status sfseg_load_features_batched(sfseg_ctx* ctx, const float* const* d_s,
+                                         const float* const* d_f, void* stream);
+sfseg_status sfseg_power_iterate_batched(sfseg_ctx* ctx, const float* const* d_s,
+                                         const float* const* d_f, float* const* d_x,
+                                         int32_t n_iters, void* stream);
+
+/* Rayleigh quotient lambda = x.Mx / x.x (Eq. 3 read as a Rayleigh quotient)
+ * and residual ||Mx - lambda x|| / ||x|| of d_x ([nf][h][w] FP32, device)
+ * with the features loaded last.  Synchronises the stream.
+ * Errors: EINVAL, ESTATE (no features loaded), ECUDA, ENONFINITE. */
+sfseg_status sfseg_rayleigh(sfseg_ctx* ctx, const float* d_x, double* lambda,
+                            double* residual, void* stream);
+
+/* One unnormalised application y = M x (Eq. 4 / Eq. 7) with the features
+ * loaded last; d_x, d_y: [nf][h][w] FP32 device, may not alias.  Stored
+ * operands go through the storage type.  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_apply(sfseg_ctx* ctx, const float* d_x, float* d_y, void* stream);
+
+/* Copy the per-step trace of the last power_iterate of video `video`
+ * (0 for a single-video context) to host arrays of capacity `cap`:
+ * Rayleigh quotient r_k, residual rho_k, norm ||M x^k||.  Any array may be
+ * NULL.  Synchronises the context's last stream.  Returns the number of
+ * steps recorded, or -1 on error. */
+int32_t sfseg_get_trace(sfseg_ctx* ctx, int32_t video, double* rayleigh,
+                        double* residual, double* norms, int32_t cap);
+
+/* Reverse mode of the last power_iterate (which must have run with
+ * SFSEG_RECORD): given d_gx = dL/dx^K ([nf][h][w] FP32, device), writes
+ *   d_gsp = dL/dsp, d_gf = dL/df (nchan = 1), d_gx0 = dL/dx0
+ * (each [nf][h][w] FP32 device, any may be NULL).  M is symmetric, so each
+ * backward step is the same stencil plus the normalisation Jacobian
+ * u = (g - x (x.g)) / ||y||.  Forward iterates are recomputed from
+ * checkpoints kept every `ckpt_every` steps.  Errors: ESTATE, EINVAL, ECUDA. */
+sfseg_status sfseg_adjoint(sfseg_ctx* ctx, const float* d_gx, float* d_gsp,
+                           float* d_gf, float* d_gx0, void* stream);
+
+/* Wait for the context's last stream and return the device-side status of
+ * the last power_iterate/rayleigh/apply: OK, EZERONORM or ENONFINITE. */
+sfseg_status sfseg_sync_status(sfseg_ctx* ctx);
+
+/* Message of the last failure on ctx (ctx may be NULL: last create failure). */
+const char* sfseg_last_error(const sfseg_ctx* ctx);
+
+/* Static name of a status code. */
+const char* sfseg_status_string(sfseg_status st);
+
+/* Number of kernel launches this context issued so far (for accounting). */
+int64_t sfseg_launch_count(const sfseg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFSEG_H */

@@ -1,0 +1,179 @@
+// prep.cu -- per-call set-up and finish kernels.
+//
+// prep_features: caller FP32 S and F (contiguous) -> internal pitched storage,
+//   sp = S^p (the unary term of Eq. 1, computed with powf), once per video.
+// prep_x:        caller FP32 x0 -> internal stored iterate, with the FP64
+//   norm ||x0|| that sets the first scale (x_hat_0 = x0 / ||x0||).
+// finish:        the unit-norm result x^K = scale * z into the caller's FP32
+//   buffer (Eq. 8 applied to the last step's output).
+#include "sfseg_launch.h"
+
+namespace sfseg {
+
+template <typename TS>
+__global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constant__ PrepFeatParams P) {
+    const VideoGeom g = P.g;
+    const long long n = g.n;
+    const long long hw = (long long)g.h * g.w;
+    TS* SPo = (TS*)P.sp_out + g.off;
+    TS* Fo = (TS*)P.f_out + g.off;
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / hw, r = i - t * hw;
+        const long long yy = r / g.w, xx = r - yy * g.w;
+        const long long o = t * g.plane + yy * g.pitch + xx;
+        const float s = P.s[i];
+        const float sp = P.s_is_sp ? s : powf(s, P.p);
+        bad |= !isfinite(s) | !isfinite(sp);
+        SPo[o] = from_f<TS>(sp);
+        for (int c = 0; c < P.nchan; ++c) {
+            const float fv = P.f[c * n + i];
+            bad |= !isfinite(fv);
+            Fo[c * P.chan_stride + o] = from_f<TS>(fv);
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.bad, 1);
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ PrepXParams P) {
+    const VideoGeom g = P.g;
+    const long long n = g.n;
+    const long long hw = (long long)g.h * g.w;
+    TS* Xo = (TS*)P.x_out + g.off;
+    float part = 0.f;
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / hw, r = i - t * hw;
+        const long long yy = r / g.w, xx = r - yy * g.w;
+        const TS xs = from_f<TS>(P.x[i]);
+        const float xv = to_f(xs);
+        bad |= !isfinite(xv);
+        Xo[t * g.plane + yy * g.pitch + xx] = xs;
+        part = fmaf(xv, xv, part);
+    }
+    bad = __syncthreads_or(bad);
+    __shared__ double sh[32];
+    __shared__ int s_last;
+    const float w = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += sh[k];
+        P.partials[blockIdx.x] = bad ? __longlong_as_double(0x7ff8000000000000LL) : s;
+        __threadfence();
+        const unsigned prev = atomicAdd(P.counter, 1u);
+        s_last = (prev + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    double xx = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) xx += __ldcg(&P.partials[b]);
+    *P.counter = 0u;
+    VState st;
+    st.tol = P.tol;
+    st.iter = 0;
+    st.final_iter = -1;
+    st.shift = 0.0;
+    st.status = 0;
+    st.done = 0;
+    st.in_norm = (isfinite(xx) && xx > 0.0) ? sqrt(xx) : 1.0;
+    const int bad_feat = P.bad_features ? *(volatile const int*)P.bad_features : 0;
+    if (P.raw) {
+        st.in_norm = 1.0;
+        st.scale = 1.0;
+        st.gain = 1.0;
+        if (!isfinite(xx) || bad_feat) { st.status = 5; st.done = 1; }
+    } else {
+        st.gain = P.gain0;
+        if (!isfinite(xx) || bad_feat) { st.status = 5; st.done = 1; st.scale = 0.0; }
+        else if (!(xx > 0.0)) { st.status = 4; st.done = 1; st.scale = 0.0; }
+        else st.scale = 1.0 / sqrt(xx);
+    }
+    P.state[P.video] = st;
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) finish_kernel(const __grid_constant__ FinishParams P) {
+    const VideoGeom g = P.g;
+    const VState st = P.state[P.video];
+    const long long n = g.n, hw = (long long)g.h * g.w;
+    const bool in_place = (st.status == 0 && st.iter == P.final_iter);
+    const float sc = (float)st.scale;
+    const TS* src = (const TS*)((st.iter & 1) ? P.buf1 : P.buf0) + g.off;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (in_place) {
+            P.out[i] = P.out[i] * sc;
+        } else {
+            const long long t = i / hw, r = i - t * hw;
+            const long long yy = r / g.w, xx = r - yy * g.w;
+            P.out[i] = (float)(st.scale * (double)to_f(src[t * g.plane + yy * g.pitch + xx]));
+        }
+    }
+}
+
+__global__ void set_ptrs_kernel(float** dst, const __grid_constant__ PtrPack pk) {
+    const int i = threadIdx.x;
+    if (i < pk.n) dst[pk.base + i] = pk.p[i];
+}
+
+static int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+int prep_x_blocks(long long n) { return grid_for(n); }
+
+cudaError_t launch_prep_features(int storage, const PrepFeatParams& P, cudaStream_t s) {
+    const int b = grid_for(P.g.n);
+    switch (storage) {
+        case 0: prep_features_kernel<float><<<b, 256, 0, s>>>(P); break;
+        case 1: prep_features_kernel<__nv_bfloat16><<<b, 256, 0, s>>>(P); break;
+        case 2: prep_features_kernel<__half><<<b, 256, 0, s>>>(P); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_prep_x(int storage, const PrepXParams& P, int blocks, cudaStream_t s) {
+    switch (storage) {
+        case 0: prep_x_kernel<float><<<blocks, 256, 0, s>>>(P); break;
+        case 1: prep_x_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(P); break;
+        case 2: prep_x_kernel<__half><<<blocks, 256, 0, s>>>(P); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s) {
+    const int b = grid_for(P.g.n);
+    switch (storage) {
+        case 0: finish_kernel<float><<<b, 256, 0, s>>>(P); break;
+        case 1: finish_kernel<__nv_bfloat16><<<b, 256, 0, s>>>(P); break;
+        case 2: finish_kernel<__half><<<b, 256, 0, s>>>(P); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_set_ptrs(float** dst, float* const* src, int n, cudaStream_t s) {
+    for (int base = 0; base < n; base += PtrPack::kMax) {
+        PtrPack pk;
+        pk.base = base;
+        pk.n = (n - base < PtrPack::kMax) ? n - base : PtrPack::kMax;
+        for (int i = 0; i < pk.n; ++i) pk.p[i] = src[base + i];
+        set_ptrs_kernel<<<1, PtrPack::kMax, 0, s>>>(dst, pk);
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sfseg

@@ -1,0 +1,596 @@
+// sfseg_api.cu -- the C-ABI of include/sfseg.h: context, validation, the
+// iteration loop (replayed as a CUDA graph) and host-side bookkeeping.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sfseg.h"
+#include "sfseg_launch.h"
+
+using namespace sfseg;
+
+struct sfseg_ctx {
+    sfseg_params prm{};
+    int nv = 0;
+    bool batched = false;
+    std::vector<VideoGeom> geo;
+    long long total = 0;        // packed elements per volume array
+    size_t elt = 4;
+    // device workspace (owned)
+    void* sp = nullptr;
+    void* f = nullptr;
+    void* xa = nullptr;
+    void* xb = nullptr;
+    VideoGeom* d_geo = nullptr;
+    VState* d_state = nullptr;
+    WorkItem* d_items = nullptr;
+    int* d_item_begin = nullptr;
+    double* d_partials = nullptr;
+    unsigned* d_counters = nullptr;
+    double* d_prep_partials = nullptr;
+    unsigned* d_prep_counter = nullptr;
+    int* d_bad = nullptr;
+    double* d_trace = nullptr;
+    int trace_cap = 0;
+    float** d_out = nullptr;
+    int n_items = 0;
+    std::vector<int> item_begin;
+    // host-side
+    float gt[2 * kMaxRt + 1], gy[2 * kMaxR + 1], gx[2 * kMaxR + 1];
+    double gsum = 1.0;
+    cudaStream_t cap_stream = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;
+    bool features = false;
+    cudaStream_t last_stream = nullptr;
+    long long launches = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static sfseg_status fail(sfseg_ctx* c, sfseg_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_err = buf;
+    return st;
+}
+
+#define CUDA_OR(ctx, call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? SFSEG_ENOMEM : SFSEG_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static sfseg_status validate(const sfseg_params* p) {
+    if (!p) return fail(nullptr, SFSEG_EINVAL, "params is NULL");
+    if (p->rt < 0 || p->rt > kMaxRt || p->ry < 0 || p->ry > kMaxR || p->rx < 0 || p->rx > kMaxR)
+        return fail(nullptr, SFSEG_EINVAL, "radii (rt,ry,rx)=(%d,%d,%d) outside [0,%d]x[0,%d]x[0,%d]",
+                    p->rt, p->ry, p->rx, kMaxRt, kMaxR, kMaxR);
+    if (!finite_pos(p->sigma_t) || !finite_pos(p->sigma_y) || !finite_pos(p->sigma_x))
+        return fail(nullptr, SFSEG_EINVAL, "sigmas must be finite and > 0");
+    if (!std::isfinite(p->alpha) || p->alpha < 0.0)
+        return fail(nullptr, SFSEG_EINVAL, "alpha must be finite and >= 0");
+    if (!std::isfinite(p->p) || p->p < 0.0)
+        return fail(nullptr, SFSEG_EINVAL, "p must be finite and >= 0");
+    if (p->storage < 0 || p->storage > 2)
+        return fail(nullptr, SFSEG_EINVAL, "storage %d is not an sfseg_dtype", p->storage);
+    if (p->nchan < 1 || p->nchan > 8)
+        return fail(nullptr, SFSEG_EINVAL, "nchan %d outside [1, 8]", p->nchan);
+    if (p->nchan != 1)
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "nchan > 1 (Eq. 9) is not built yet");
+    if (p->ckpt_every < 0) return fail(nullptr, SFSEG_EINVAL, "ckpt_every must be >= 0");
+    return SFSEG_OK;
+}
+
+static void free_ctx(sfseg_ctx* c) {
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+    void* ptrs[] = {c->sp, c->f, c->xa, c->xb, c->d_geo, c->d_state, c->d_items, c->d_item_begin,
+                    c->d_partials, c->d_counters, c->d_prep_partials, c->d_prep_counter, c->d_bad,
+                    c->d_trace, c->d_out};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+static void host_taps(int r, double sigma, float* g, double* sum) {
+    double s = 0.0;
+    for (int d = -r; d <= r; ++d) {
+        const double v = std::exp(-(double)d * d / (2.0 * sigma * sigma));
+        g[d + r] = (float)v;
+        s += (double)(float)v;
+    }
+    *sum *= s;
+}
+
+static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* dims, bool batched,
+                                sfseg_ctx** out) {
+    if (!out) return fail(nullptr, SFSEG_EINVAL, "out is NULL");
+    *out = nullptr;
+    sfseg_status st = validate(prm);
+    if (st != SFSEG_OK) return st;
+    if (nv < 1) return fail(nullptr, SFSEG_EINVAL, "n_videos must be >= 1");
+    for (int v = 0; v < nv; ++v)
+        if (dims[3 * v] < 1 || dims[3 * v + 1] < 1 || dims[3 * v + 2] < 1)
+            return fail(nullptr, SFSEG_EINVAL, "video %d: dims (%d,%d,%d) must be >= 1", v,
+                        dims[3 * v], dims[3 * v + 1], dims[3 * v + 2]);
+    sfseg_ctx* c = new sfseg_ctx();
+    c->prm = *prm;
+    c->nv = nv;
+    c->batched = batched;
+    c->elt = prm->storage == SFSEG_F32 ? 4 : 2;
+    const long long align = 256 / (long long)c->elt;
+    long long off = 0;
+    int tx, ty;
+    generic_tile(&tx, &ty);
+    std::vector<WorkItem> items;
+    for (int v = 0; v < nv; ++v) {
+        VideoGeom g;
+        g.nf = dims[3 * v];
+        g.h = dims[3 * v + 1];
+        g.w = dims[3 * v + 2];
+        g.pitch = (g.w + 7) / 8 * 8;
+        g.plane = (long long)g.h * g.pitch;
+        g.off = off;
+        g.n = (long long)g.nf * g.h * g.w;
+        off += (g.nf * g.plane + align - 1) / align * align;
+        c->geo.push_back(g);
+        c->item_begin.push_back((int)items.size());
+        for (int y0 = 0; y0 < g.h; y0 += ty)
+            for (int x0 = 0; x0 < g.w; x0 += tx) {
+                WorkItem it{};
+                it.video = v;
+                it.x0 = x0;
+                it.y0 = y0;
+                it.t0 = 0;
+                it.t1 = g.nf;
+                items.push_back(it);
+            }
+    }
+    c->item_begin.push_back((int)items.size());
+    c->total = off;
+    c->n_items = (int)items.size();
+    c->gsum = 1.0;
+    host_taps(prm->rt, prm->sigma_t, c->gt, &c->gsum);
+    host_taps(prm->ry, prm->sigma_y, c->gy, &c->gsum);
+    host_taps(prm->rx, prm->sigma_x, c->gx, &c->gsum);
+
+#define ALLOC(ptr, bytes)                                                                 \
+    do {                                                                                  \
+        cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                             \
+        if (e_ != cudaSuccess) {                                                          \
+            fail(nullptr, SFSEG_ENOMEM, "cudaMalloc(%zu): %s", (size_t)(bytes),           \
+                 cudaGetErrorString(e_));                                                 \
+            free_ctx(c);                                                                  \
+            return SFSEG_ENOMEM;                                                          \
+        }                                                                                 \
+    } while (0)
+    const size_t vol = (size_t)c->total * c->elt;
+    ALLOC(c->sp, vol);
+    ALLOC(c->f, vol * prm->nchan);
+    ALLOC(c->xa, vol);
+    ALLOC(c->xb, vol);
+    ALLOC(c->d_geo, sizeof(VideoGeom) * nv);
+    ALLOC(c->d_state, sizeof(VState) * nv);
+    ALLOC(c->d_items, sizeof(WorkItem) * items.size());
+    ALLOC(c->d_item_begin, sizeof(int) * (nv + 1));
+    ALLOC(c->d_partials, sizeof(double) * kRed * items.size());
+    ALLOC(c->d_counters, sizeof(unsigned) * nv);
+    ALLOC(c->d_prep_partials, sizeof(double) * prep_x_blocks(1LL << 40));
+    ALLOC(c->d_prep_counter, sizeof(unsigned));
+    ALLOC(c->d_bad, sizeof(int));
+    ALLOC(c->d_out, sizeof(float*) * nv);
+#undef ALLOC
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemset(c->sp, 0, vol);
+    if (e == cudaSuccess) e = cudaMemset(c->f, 0, vol * prm->nchan);
+    if (e == cudaSuccess) e = cudaMemset(c->xa, 0, vol);
+    if (e == cudaSuccess) e = cudaMemset(c->xb, 0, vol);
+    if (e == cudaSuccess) e = cudaMemset(c->d_state, 0, sizeof(VState) * nv);
+    if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(unsigned) * nv);
+    if (e == cudaSuccess) e = cudaMemset(c->d_prep_counter, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(c->d_bad, 0, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_geo, c->geo.data(), sizeof(VideoGeom) * nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_item_begin, c->item_begin.data(), sizeof(int) * (nv + 1),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = setup_step_generic(prm->rt, prm->ry, prm->rx);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fail(nullptr, SFSEG_ECUDA, "context set-up: %s", cudaGetErrorString(e));
+        free_ctx(c);
+        return SFSEG_ECUDA;
+    }
+    *out = c;
+    return SFSEG_OK;
+}
+
+static sfseg_status ensure_trace(sfseg_ctx* c, int K) {
+    if (K <= c->trace_cap) return SFSEG_OK;
+    int cap = c->trace_cap ? c->trace_cap : 64;
+    while (cap < K) cap *= 2;
+    double* t = nullptr;
+    CUDA_OR(c, cudaDeviceSynchronize());
+    CUDA_OR(c, cudaMalloc((void**)&t, sizeof(double) * 3 * (size_t)cap * c->nv));
+    CUDA_OR(c, cudaMemset(t, 0, sizeof(double) * 3 * (size_t)cap * c->nv));
+    if (c->d_trace) cudaFree(c->d_trace);
+    c->d_trace = t;
+    c->trace_cap = cap;
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);   // they captured the old pointer
+    c->graphs.clear();
+    return SFSEG_OK;
+}
+
+static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store) {
+    StepParams P{};
+    P.x_in = (k & 1) ? c->xb : c->xa;
+    P.z_out = (store && !final_out) ? ((k & 1) ? c->xa : c->xb) : nullptr;
+    P.final_out = final_out ? c->d_out : nullptr;
+    P.sp = c->sp;
+    P.f = c->f;
+    P.geo = c->d_geo;
+    P.state = c->d_state;
+    P.items = c->d_items;
+    P.item_begin = c->d_item_begin;
+    P.partials = c->d_partials;
+    P.counters = c->d_counters;
+    P.trace = c->d_trace;
+    P.trace_cap = c->trace_cap;
+    P.n_items = c->n_items;
+    P.alpha = (float)c->prm.alpha;
+    P.rt = c->prm.rt;
+    P.ry = c->prm.ry;
+    P.rx = c->prm.rx;
+    memcpy(P.gt, c->gt, sizeof c->gt);
+    memcpy(P.gy, c->gy, sizeof c->gy);
+    memcpy(P.gx, c->gx, sizeof c->gx);
+    return P;
+}
+
+static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s) {
+    StepParams P = step_params(c, k, final_out, store);
+    c->launches += 1;
+    return launch_step_generic(c->prm.storage, P, c->n_items, s);
+}
+
+// Steps [0, n) that store into the internal ping-pong buffers: one CUDA
+// graph per n, captured on the context's own stream and replayed on the
+// caller's stream.
+static sfseg_status run_steps(sfseg_ctx* c, int n, cudaStream_t s) {
+    if (n <= 0) return SFSEG_OK;
+    if (c->prm.flags & SFSEG_NO_GRAPH) {
+        for (int k = 0; k < n; ++k) CUDA_OR(c, launch_step(c, k, false, true, s));
+        return SFSEG_OK;
+    }
+    auto it = c->graphs.find(n);
+    if (it == c->graphs.end()) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const long long before = c->launches;
+        CUDA_OR(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < n && le == cudaSuccess; ++k) le = launch_step(c, k, false, true, c->cap_stream);
+        cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+        c->launches = before;
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(c, SFSEG_ECUDA, "graph capture: %s / %s", cudaGetErrorString(le),
+                        cudaGetErrorString(ee));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(c, SFSEG_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+        if (c->graphs.size() >= 16) {
+            cudaGraphExecDestroy(c->graphs.begin()->second);
+            c->graphs.erase(c->graphs.begin());
+        }
+        it = c->graphs.emplace(n, exec).first;
+    }
+    CUDA_OR(c, cudaGraphLaunch(it->second, s));
+    c->launches += n;
+    return SFSEG_OK;
+}
+
+static sfseg_status load_features_impl(sfseg_ctx* c, const float* const* d_s, const float* const* d_f,
+                                       cudaStream_t s) {
+    for (int v = 0; v < c->nv; ++v)
+        if (!d_s[v] || !d_f[v]) return fail(c, SFSEG_EINVAL, "video %d: NULL feature pointer", v);
+    CUDA_OR(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), s));
+    for (int v = 0; v < c->nv; ++v) {
+        PrepFeatParams P{};
+        P.s = d_s[v];
+        P.f = d_f[v];
+        P.sp_out = c->sp;
+        P.f_out = c->f;
+        P.chan_stride = c->total;
+        P.g = c->geo[v];
+        P.nchan = c->prm.nchan;
+        P.p = (float)c->prm.p;
+        P.s_is_sp = (c->prm.flags & SFSEG_S_IS_SP) ? 1 : 0;
+        P.bad = c->d_bad;
+        CUDA_OR(c, launch_prep_features(c->prm.storage, P, s));
+        c->launches += 1;
+    }
+    c->features = true;
+    return SFSEG_OK;
+}
+
+static sfseg_status prep_x(sfseg_ctx* c, int v, const float* d_x, bool raw, double tol, cudaStream_t s) {
+    PrepXParams P{};
+    P.x = d_x;
+    P.x_out = c->xa;
+    P.g = c->geo[v];
+    P.video = v;
+    P.raw = raw ? 1 : 0;
+    P.gain0 = std::exp2(std::rint(std::log2(std::sqrt((double)c->geo[v].n) / c->gsum)));
+    P.tol = tol;
+    P.bad_features = c->d_bad;
+    P.state = c->d_state;
+    P.partials = c->d_prep_partials;
+    P.counter = c->d_prep_counter;
+    CUDA_OR(c, launch_prep_x(c->prm.storage, P, prep_x_blocks(c->geo[v].n), s));
+    c->launches += 1;
+    return SFSEG_OK;
+}
+
+static sfseg_status device_status(sfseg_ctx* c, cudaStream_t s, std::vector<VState>* out) {
+    std::vector<VState> st(c->nv);
+    CUDA_OR(c, cudaStreamSynchronize(s));
+    CUDA_OR(c, cudaMemcpy(st.data(), c->d_state, sizeof(VState) * c->nv, cudaMemcpyDeviceToHost));
+    if (out) *out = st;
+    for (int v = 0; v < c->nv; ++v)
+        if (st[v].status != 0)
+            return fail(c, (sfseg_status)st[v].status, "video %d: %s at step %d", v,
+                        sfseg_status_string((sfseg_status)st[v].status), st[v].iter);
+    return SFSEG_OK;
+}
+
+static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float* const* d_x,
+                                 int K, double tol, int32_t* iters_done, cudaStream_t s) {
+    if (K < 0) return fail(c, SFSEG_EINVAL, "n_iters must be >= 0");
+    if (!std::isfinite(tol) || tol < 0.0) return fail(c, SFSEG_EINVAL, "tol must be finite and >= 0");
+    if (!c->features) return fail(c, SFSEG_ESTATE, "no features loaded");
+    for (int v = 0; v < c->nv; ++v)
+        if (!d_x[v]) return fail(c, SFSEG_EINVAL, "video %d: NULL x pointer", v);
+    sfseg_status st = ensure_trace(c, K > 0 ? K : 1);
+    if (st != SFSEG_OK) return st;
+    for (int v = 0; v < c->nv; ++v) {
+        st = prep_x(c, v, d_x_in[v], false, tol, s);
+        if (st != SFSEG_OK) return st;
+    }
+    const bool final_mode = (K > 0 && tol == 0.0);
+    st = run_steps(c, final_mode ? K - 1 : K, s);
+    if (st != SFSEG_OK) return st;
+    if (final_mode) {
+        CUDA_OR(c, launch_set_ptrs(c->d_out, d_x, c->nv, s));
+        CUDA_OR(c, launch_step(c, K - 1, true, true, s));
+        c->launches += 1;   // set_ptrs
+    }
+    for (int v = 0; v < c->nv; ++v) {
+        FinishParams F{};
+        F.out = d_x[v];
+        F.buf0 = c->xa;
+        F.buf1 = c->xb;
+        F.g = c->geo[v];
+        F.state = c->d_state;
+        F.video = v;
+        F.final_iter = final_mode ? K : -1;
+        CUDA_OR(c, launch_finish(c->prm.storage, F, s));
+        c->launches += 1;
+    }
+    c->last_stream = s;
+    if (iters_done) {
+        std::vector<VState> vs;
+        st = device_status(c, s, &vs);
+        *iters_done = vs[0].iter;
+        return st;
+    }
+    return SFSEG_OK;
+}
+
+// ======================================================================= C-ABI
+extern "C" {
+
+void sfseg_default_params(sfseg_params* p, int32_t nf, int32_t h, int32_t w) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->nf = nf;
+    p->h = h;
+    p->w = w;
+    p->rt = 2;
+    p->ry = 5;
+    p->rx = 5;
+    p->sigma_t = 1.5;
+    p->sigma_y = 3.0;
+    p->sigma_x = 3.0;
+    p->alpha = 1.0;
+    p->p = 0.1;
+    p->storage = SFSEG_F32;
+    p->flags = 0;
+    p->nchan = 1;
+    p->ckpt_every = 8;
+}
+
+sfseg_status sfseg_create(const sfseg_params* prm, sfseg_ctx** out) {
+    if (!prm) return fail(nullptr, SFSEG_EINVAL, "params is NULL");
+    int32_t dims[3] = {prm->nf, prm->h, prm->w};
+    return create_impl(prm, 1, dims, false, out);
+}
+
+sfseg_status sfseg_create_batched(const sfseg_params* prm, int32_t n_videos, const int32_t* dims,
+                                  sfseg_ctx** out) {
+    if (!dims) return fail(nullptr, SFSEG_EINVAL, "dims is NULL");
+    return create_impl(prm, n_videos, dims, true, out);
+}
+
+void sfseg_destroy(sfseg_ctx* ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+}
+
+sfseg_status sfseg_load_features(sfseg_ctx* c, const float* d_s, const float* d_f, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (c->batched) return fail(c, SFSEG_EINVAL, "batched context: use sfseg_load_features_batched");
+    return load_features_impl(c, &d_s, &d_f, (cudaStream_t)stream);
+}
+
+sfseg_status sfseg_load_features_batched(sfseg_ctx* c, const float* const* d_s,
+                                         const float* const* d_f, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (!d_s || !d_f) return fail(c, SFSEG_EINVAL, "NULL pointer array");
+    return load_features_impl(c, d_s, d_f, (cudaStream_t)stream);
+}
+
+sfseg_status sfseg_power_iterate(sfseg_ctx* c, const float* d_s, const float* d_f, float* d_x,
+                                 int32_t n_iters, double tol, int32_t* iters_done, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (c->batched) return fail(c, SFSEG_EINVAL, "batched context: use sfseg_power_iterate_batched");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((d_s == nullptr) != (d_f == nullptr))
+        return fail(c, SFSEG_EINVAL, "pass both d_s and d_f, or neither");
+    if (d_s) {
+        sfseg_status st = load_features_impl(c, &d_s, &d_f, s);
+        if (st != SFSEG_OK) return st;
+    }
+    const float* xin = d_x;
+    return iterate_impl(c, &xin, &d_x, n_iters, tol, iters_done, s);
+}
+
+sfseg_status sfseg_power_iterate_batched(sfseg_ctx* c, const float* const* d_s,
+                                         const float* const* d_f, float* const* d_x,
+                                         int32_t n_iters, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((d_s == nullptr) != (d_f == nullptr))
+        return fail(c, SFSEG_EINVAL, "pass both d_s and d_f, or neither");
+    if (d_s) {
+        sfseg_status st = load_features_impl(c, d_s, d_f, s);
+        if (st != SFSEG_OK) return st;
+    }
+    std::vector<const float*> xin(d_x, d_x + c->nv);
+    return iterate_impl(c, xin.data(), d_x, n_iters, 0.0, nullptr, s);
+}
+
+sfseg_status sfseg_rayleigh(sfseg_ctx* c, const float* d_x, double* lambda, double* residual,
+                            void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (c->batched) return fail(c, SFSEG_EINVAL, "rayleigh needs a single-video context");
+    if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
+    if (!c->features) return fail(c, SFSEG_ESTATE, "no features loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    sfseg_status st = ensure_trace(c, 1);
+    if (st != SFSEG_OK) return st;
+    st = prep_x(c, 0, d_x, false, 0.0, s);
+    if (st != SFSEG_OK) return st;
+    CUDA_OR(c, launch_step(c, 0, false, false, s));
+    st = device_status(c, s, nullptr);
+    if (st != SFSEG_OK) return st;
+    double row[3];
+    CUDA_OR(c, cudaMemcpy(row, c->d_trace, sizeof row, cudaMemcpyDeviceToHost));
+    if (lambda) *lambda = row[0];
+    if (residual) *residual = row[1];
+    c->last_stream = s;
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_apply(sfseg_ctx* c, const float* d_x, float* d_y, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (c->batched) return fail(c, SFSEG_EINVAL, "apply needs a single-video context");
+    if (!d_x || !d_y) return fail(c, SFSEG_EINVAL, "NULL pointer");
+    if (d_x == d_y) return fail(c, SFSEG_EINVAL, "d_x and d_y may not alias");
+    if (!c->features) return fail(c, SFSEG_ESTATE, "no features loaded");
+    cudaStream_t s = (cudaStream_t)stream;
+    sfseg_status st = ensure_trace(c, 1);
+    if (st != SFSEG_OK) return st;
+    st = prep_x(c, 0, d_x, true, 0.0, s);
+    if (st != SFSEG_OK) return st;
+    CUDA_OR(c, launch_set_ptrs(c->d_out, &d_y, 1, s));
+    CUDA_OR(c, launch_step(c, 0, true, true, s));
+    c->launches += 1;
+    c->last_stream = s;
+    return SFSEG_OK;
+}
+
+int32_t sfseg_get_trace(sfseg_ctx* c, int32_t video, double* rayleigh, double* residual,
+                        double* norms, int32_t cap) {
+    if (!c) return -1;
+    if (video < 0 || video >= c->nv || cap < 0) {
+        fail(c, SFSEG_EINVAL, "bad video index or capacity");
+        return -1;
+    }
+    if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) {
+        fail(c, SFSEG_ECUDA, "stream synchronise failed");
+        return -1;
+    }
+    VState st;
+    if (cudaMemcpy(&st, c->d_state + video, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        fail(c, SFSEG_ECUDA, "state copy failed");
+        return -1;
+    }
+    int n = st.iter < c->trace_cap ? st.iter : c->trace_cap;
+    if (n > cap) n = cap;
+    if (n > 0) {
+        std::vector<double> rows(3 * (size_t)n);
+        if (cudaMemcpy(rows.data(), c->d_trace + 3 * (size_t)video * c->trace_cap,
+                       sizeof(double) * 3 * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fail(c, SFSEG_ECUDA, "trace copy failed");
+            return -1;
+        }
+        for (int k = 0; k < n; ++k) {
+            if (rayleigh) rayleigh[k] = rows[3 * k];
+            if (residual) residual[k] = rows[3 * k + 1];
+            if (norms) norms[k] = rows[3 * k + 2];
+        }
+    }
+    return n;
+}
+
+sfseg_status sfseg_adjoint(sfseg_ctx* c, const float*, float*, float*, float*, void*) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    return fail(c, SFSEG_EUNSUPPORTED, "adjoint is not built yet");
+}
+
+sfseg_status sfseg_sync_status(sfseg_ctx* c) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    return device_status(c, c->last_stream, nullptr);
+}
+
+const char* sfseg_last_error(const sfseg_ctx* c) {
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+const char* sfseg_status_string(sfseg_status st) {
+    switch (st) {
+        case SFSEG_OK: return "SFSEG_OK";
+        case SFSEG_EINVAL: return "SFSEG_EINVAL";
+        case SFSEG_ENOMEM: return "SFSEG_ENOMEM";
+        case SFSEG_ECUDA: return "SFSEG_ECUDA";
+        case SFSEG_EZERONORM: return "SFSEG_EZERONORM";
+        case SFSEG_ENONFINITE: return "SFSEG_ENONFINITE";
+        case SFSEG_ETIMEOUT: return "SFSEG_ETIMEOUT";
+        case SFSEG_EUNSUPPORTED: return "SFSEG_EUNSUPPORTED";
+        case SFSEG_ESTATE: return "SFSEG_ESTATE";
+    }
+    return "SFSEG_UNKNOWN";
+}
+
+int64_t sfseg_launch_count(const sfseg_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

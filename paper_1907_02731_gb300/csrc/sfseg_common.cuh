@@ -1,0 +1,195 @@
+// sfseg_common.cuh -- types and device helpers shared by the SFSeg kernels.
+//
+// Internal layout in HBM (one packed allocation per array, all videos of a
+// context back to back, each video 256-byte aligned):
+//   sp, f, x_a, x_b : [nf][h][pitch] in the storage type, pitch = w rounded
+//                     up to 8 elements (16-byte rows for FP32, BF16 and FP16),
+//                     the pad columns are zero and never read as data.
+// The iterate is stored unnormalised: x_hat = scale * x_stored (deferred
+// normalisation, Eq. 8), and each step stores z = gain * M x_hat with a
+// power-of-two gain that keeps the stored values near RMS 1 (FP16 range).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfseg {
+
+constexpr int kMaxR = 16;       // largest spatial radius
+constexpr int kMaxRt = 8;       // largest temporal radius
+constexpr int kRed = 4;         // reductions per step: z.z, xh.z, xh.xh, |z - s xh|^2
+
+struct VideoGeom {
+    int nf, h, w, pitch;        // pitch in elements
+    long long plane;            // h * pitch
+    long long off;              // element offset of this video in the packed arrays
+    long long n;                // nf * h * w (voxels)
+};
+
+// Per-video device state, updated by the last CTA of each step (finalize).
+struct VState {
+    double scale;               // x_hat = scale * stored iterate
+    double gain;                // the step stores z = gain * (M x_hat)
+    double shift;               // gain * r_{k-1}: shift of the residual sum
+    double tol;                 // early-stop tolerance on rho/r (0 = off)
+    int iter;                   // completed steps
+    int done;                   // 1: converged or failed, later steps skip
+    int status;                 // sfseg_status of the device-side checks
+    int final_iter;             // step count whose output went to the caller buffer
+    double in_norm;             // ||x^k|| of the caller's scale: ||x0|| before step 0, then 1
+};
+
+// One CTA's share of a step: a (x0, y0) tile of one video over frames [t0, t1).
+struct WorkItem {
+    int video, x0, y0, t0, t1;
+    int pad[3];
+};
+
+struct StepParams {
+    const void* x_in;           // packed stored iterate (storage type)
+    void* z_out;                // packed output (storage type), or null
+    float* const* final_out;    // per-video contiguous FP32 output, or null
+    const void* sp;
+    const void* f;
+    const VideoGeom* geo;
+    VState* state;
+    const WorkItem* items;
+    const int* item_begin;      // [n_videos + 1]: items of video v are [b[v], b[v+1])
+    double* partials;           // [n_items][kRed]
+    unsigned* counters;         // [n_videos]
+    double* trace;              // [n_videos][trace_cap][3]: r_k, rho_k, ||M x_hat||
+    int trace_cap;
+    int n_items;
+    float alpha;
+    int rt, ry, rx;
+    float gt[2 * kMaxRt + 1];
+    float gy[2 * kMaxR + 1];
+    float gx[2 * kMaxR + 1];
+};
+
+// ---------------------------------------------------------------- storage
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+// ------------------------------------------------------------ reductions
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Adds the warp's FP32 partials into lane 0's FP64 accumulators and clears them.
+__device__ __forceinline__ void warp_flush(float (&p)[kRed], double (&acc)[kRed]) {
+#pragma unroll
+    for (int c = 0; c < kRed; ++c) {
+        float s = warp_sum(p[c]);
+        if ((threadIdx.x & 31) == 0) acc[c] += (double)s;
+        p[c] = 0.f;
+    }
+}
+
+// Block-wide FP64 sum of lane-0 accumulators, result valid in thread 0.
+// Fixed order (deterministic).  `sh` must hold kRed * (blockDim/32) doubles.
+__device__ __forceinline__ void block_sum_lane0(double (&acc)[kRed], double* sh) {
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < kRed; ++c) sh[warp * kRed + c] = acc[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < kRed; ++c) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[w * kRed + c];
+            acc[c] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// The step's scalar update (Eq. 3 Rayleigh quotient, residual, Eq. 8 norm),
+// from the FP64 sums S = (z.z, xh.z, xh.xh, |z - shift xh|^2) of video v.
+// Runs in one thread.
+__device__ inline void finish_step(VState* st, double* trace_row, const double (&S)[kRed],
+                                   long long n_vox) {
+    const double zz = S[0], xz = S[1], xx = S[2], dd = S[3];
+    const double gain = st->gain, sig = st->shift;
+    if (!(isfinite(zz) && isfinite(xz) && isfinite(xx) && isfinite(dd))) {
+        st->status = 5;   // SFSEG_ENONFINITE
+        st->done = 1;
+        return;
+    }
+    if (!(zz > 0.0) || !(xx > 0.0)) {
+        st->status = 4;   // SFSEG_EZERONORM
+        st->done = 1;
+        return;
+    }
+    const double ny = sqrt(zz) / gain;          // ||M x_hat||, x_hat of unit norm
+    const double rz = xz / xx;                   // Rayleigh quotient of z = gain * M x_hat
+    const double r = rz / gain;
+    // ||z - rz xh||^2 = ||z - sig xh||^2 - (rz - sig)^2 xh.xh  (exact identity)
+    double e = dd - (rz - sig) * (rz - sig) * xx;
+    if (e < 0.0) e = 0.0;
+    const double rho = sqrt(e / xx) / gain;
+    if (trace_row) {
+        trace_row[0] = r;
+        trace_row[1] = rho;
+        trace_row[2] = ny * st->in_norm;        // ||M x^k|| at the caller's scale of x^k
+    }
+    st->in_norm = 1.0;
+    st->scale = 1.0 / sqrt(zz);
+    const double target = sqrt((double)n_vox) * sqrt(xx) / ny;
+    st->gain = exp2(rint(log2(target)));
+    st->shift = st->gain * r;
+    st->iter += 1;
+    if (st->tol > 0.0 && rho < st->tol * fabs(r)) st->done = 1;
+}
+
+// After a CTA of video v stored its FP64 partials (thread 0), the last CTA
+// of that video to arrive reduces all of them (fixed order) and runs
+// finish_step.  No CTA ever waits on another: the last one does the work.
+__device__ inline void arrive_and_finalize(const StepParams& P, int v, double* sh) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned cnt = (unsigned)(P.item_begin[v + 1] - P.item_begin[v]);
+        const unsigned prev = atomicAdd(&P.counters[v], 1u);
+        s_last = (prev + 1u == cnt);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int b = P.item_begin[v], e = P.item_begin[v + 1];
+    double acc[kRed] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = b + (int)threadIdx.x; i < e; i += blockDim.x)
+        for (int c = 0; c < kRed; ++c) acc[c] += __ldcg(&P.partials[(long long)i * kRed + c]);
+    // tree over threads in shared memory (fixed order)
+    double* red = sh;   // blockDim * kRed doubles
+    for (int c = 0; c < kRed; ++c) red[c * blockDim.x + threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < kRed; ++c)
+                red[c * blockDim.x + threadIdx.x] += red[c * blockDim.x + threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double S[kRed];
+        for (int c = 0; c < kRed; ++c) S[c] = red[c * blockDim.x];
+        VState* st = P.state + v;
+        const int k = st->iter;
+        double* row = (k < P.trace_cap) ? P.trace + ((long long)v * P.trace_cap + k) * 3 : nullptr;
+        finish_step(st, row, S, P.geo[v].n);
+        P.counters[v] = 0u;
+    }
+}
+
+}  // namespace sfseg

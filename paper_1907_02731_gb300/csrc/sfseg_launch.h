@@ -1,0 +1,69 @@
+// sfseg_launch.h -- host-side launchers of the SFSeg kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "sfseg_common.cuh"
+
+namespace sfseg {
+
+// ------------------------------------------------------------- prepare
+struct PrepFeatParams {
+    const float* s;             // caller [nf][h][w] FP32
+    const float* f;             // caller [nchan][nf][h][w] FP32
+    void* sp_out;               // internal pitched, storage type
+    void* f_out;                // internal pitched, storage type ([nchan] volumes)
+    long long chan_stride;      // elements between channel volumes of f_out
+    VideoGeom g;
+    int nchan;
+    float p;
+    int s_is_sp;
+    int* bad;                   // set to 1 if a non-finite input is seen
+};
+
+struct PrepXParams {
+    const float* x;             // caller [nf][h][w] FP32
+    void* x_out;                // internal pitched, storage type
+    VideoGeom g;
+    int video;
+    int raw;                    // 1: scale = gain = 1 (unnormalised apply)
+    double gain0;               // first step's gain
+    double tol;
+    const int* bad_features;    // nullable
+    VState* state;
+    double* partials;           // [gridDim.x]
+    unsigned* counter;
+};
+
+// Up to kMax device pointers passed by value to a tiny kernel that writes
+// them into a device array (safe inside stream order, no host staging).
+struct PtrPack {
+    static constexpr int kMax = 64;
+    int base, n;
+    float* p[kMax];
+};
+
+struct FinishParams {
+    float* out;                 // caller [nf][h][w] FP32
+    const void* buf0;           // packed stored iterates
+    const void* buf1;
+    VideoGeom g;
+    const VState* state;
+    int video;
+    int final_iter;             // iter value meaning "the last step wrote `out`"
+};
+
+cudaError_t launch_prep_features(int storage, const PrepFeatParams& P, cudaStream_t s);
+cudaError_t launch_prep_x(int storage, const PrepXParams& P, int blocks, cudaStream_t s);
+cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s);
+cudaError_t launch_set_ptrs(float** dst, float* const* src, int n, cudaStream_t s);
+int prep_x_blocks(long long n);
+
+// ---------------------------------------------------------------- steps
+size_t generic_smem_bytes(int rt, int ry, int rx);
+void generic_tile(int* tx, int* ty);
+cudaError_t setup_step_generic(int rt, int ry, int rx);
+cudaError_t launch_step_generic(int storage, const StepParams& P, int n_items, cudaStream_t s);
+
+}  // namespace sfseg

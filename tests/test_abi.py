@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol include/sfseg.h
+declares; host-side validation works without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1907_02731_gb300 as sf
+from paper_1907_02731_gb300 import build as sfbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(sfseg_[a-z_0-9]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    sfbuild.build()
+    return sf.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert names == set(sf.EXPORTS)
+
+
+def test_default_params_and_status_strings(lib):
+    p = sf.sfseg_default_params(72, 480, 854)
+    assert (p.nf, p.h, p.w, p.rt, p.ry, p.rx) == (72, 480, 854, 2, 5, 5)
+    assert (p.sigma_t, p.sigma_y, p.alpha, p.p, p.nchan) == (1.5, 3.0, 1.0, 0.1, 1)
+    assert sf.sfseg_status_string(sf.SFSEG_EZERONORM) == "SFSEG_EZERONORM"
+    assert sf.sfseg_status_string(99) == "SFSEG_UNKNOWN"
+
+
+@pytest.mark.parametrize("field,value", [("rx", -1), ("ry", 17), ("rt", 9), ("sigma_t", 0.0),
+                                         ("alpha", -1.0), ("p", float("nan")), ("storage", 3),
+                                         ("nf", 0), ("w", -5), ("nchan", 0)])
+def test_create_rejects_bad_params(lib, field, value):
+    """Validation happens on the host before any device call."""
+    p = sf.sfseg_default_params(4, 8, 8)
+    setattr(p, field, value)
+    with pytest.raises(sf.SFSegError) as ei:
+        sf.sfseg_create(p)
+    assert ei.value.status == sf.SFSEG_EINVAL
+    assert sf.sfseg_last_error(None)
+
+
+def test_null_context_calls(lib):
+    assert lib.sfseg_power_iterate(None, None, None, None, 1, 0.0, None, None) == sf.SFSEG_EINVAL
+    assert lib.sfseg_get_trace(None, 0, None, None, None, 0) == -1
+    lib.sfseg_destroy(None)
+    assert lib.sfseg_launch_count(None) == 0

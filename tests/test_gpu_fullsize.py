@@ -1,0 +1,159 @@
+"""Parity at the paper's video size (854x480, 72 frames, 11x11x5 Gaussian),
+in the launch configuration the benchmark times."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1907_02731_gb300 as sf
+from paper_1907_02731_gb300 import inputs
+
+from _helpers import TOL_F32, TOL_LOWP, rel_l2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+WL = inputs.WORKLOADS["video_72x480x854"]
+RADII = (WL.rt, WL.ry, WL.rx)
+SIG = (WL.sigma_t, WL.sigma_xy, WL.sigma_xy)
+SHAPE = (WL.nf, WL.h, WL.w)
+
+
+@pytest.fixture(scope="module")
+def video():
+    f, _ = inputs.workload_video(WL.name)
+    return f
+
+
+def _toeplitz(n, g):
+    r = len(g) // 2
+    d = np.arange(n)[:, None] - np.arange(n)[None, :]
+    return np.where(np.abs(d) <= r, np.asarray(g)[np.clip(d + r, 0, 2 * r)], 0.0)
+
+
+def test_fullsize_constant_feature_closed_form(cuda_device):
+    """f == c (S = F): M = c^{2p} G_t (x) G_y (x) G_x, so from a separable x0
+    every iterate is separable: x^K = (T_t^K a_t) (x) (T_y^K a_y) (x) (T_x^K a_x),
+    each factor normalised, computed in FP64 with 1D matrices; r_k is the
+    product of the 1D Rayleigh quotients times c^{2p}."""
+    import torch
+    c, K = 0.6, WL.iters
+    rng = np.random.default_rng(21)
+    a = [0.5 + rng.random(n) for n in SHAPE]
+    x0 = np.einsum("i,j,k->ijk", *[v.astype(np.float32) for v in a]).astype(np.float32)
+    feat = np.full(SHAPE, c, np.float32)
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p)
+    x = eng.power_iterate(to_dev(feat), to_dev(feat), to_dev(x0), K)
+    torch.cuda.synchronize()
+    tr = eng.trace()
+    eng.close()
+    T = [_toeplitz(n, oracle.taps(r, s)) for n, r, s in zip(SHAPE, RADII, SIG)]
+    v = [np.asarray(ai, np.float64) / np.linalg.norm(ai) for ai in a]
+    lam = []
+    for k in range(K):
+        r = (c ** (2 * WL.p))
+        for i in range(3):
+            y = T[i] @ v[i]
+            r *= float(v[i] @ y)
+            v[i] = y / np.linalg.norm(y)
+        lam.append(r)
+    xref = np.einsum("i,j,k->ijk", *v)
+    assert rel_l2(x.cpu().numpy(), xref) < TOL_F32
+    np.testing.assert_allclose(tr["rayleigh"], lam, rtol=2e-6)
+
+
+def test_fullsize_sampled_one_step(cuda_device, video):
+    """y = M f at 4096 sampled voxels (plus corners and edges) vs the oracle,
+    evaluated edge by edge at each sample."""
+    f = video
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p)
+    d = to_dev(f)
+    eng.load_features(d, d)
+    y = eng.apply(d).cpu().numpy().ravel()
+    eng.close()
+    rng = np.random.default_rng(22)
+    nf, h, w = SHAPE
+    pts = [(t, yy, xx) for t in (0, 1, nf - 2, nf - 1) for yy in (0, 4, h // 2, h - 1)
+           for xx in (0, 5, 31, 32, w // 2, w - 6, w - 1)]
+    idx = np.concatenate([rng.integers(0, f.size, 4096),
+                          np.array([(t * h + yy) * w + xx for t, yy, xx in pts])])
+    sp = oracle.unary(f, WL.p)
+    ref = oracle.apply_M_at(sp, f, f, RADII, SIG, WL.alpha, idx)
+    assert rel_l2(y[idx], ref) < 1e-6
+    assert np.max(np.abs(y[idx] - ref) / np.abs(ref).max()) < 1e-6
+
+
+def test_fullsize_three_steps_full_vector(cuda_device, video):
+    """Three full power steps at full size against the explicit oracle."""
+    import torch
+    f = video
+    K = 3
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p)
+    d = to_dev(f)
+    x = eng.power_iterate(d, d, d, K)
+    torch.cuda.synchronize()
+    tr = eng.trace()
+    eng.close()
+    ref = oracle.power_iterate(oracle.unary(f, WL.p), f, f, K, RADII, SIG, WL.alpha)
+    assert rel_l2(x.cpu().numpy(), ref["x"]) < TOL_F32
+    np.testing.assert_allclose(tr["rayleigh"], ref["rayleigh"], rtol=1e-6)
+    np.testing.assert_allclose(tr["residual"], ref["residual"], rtol=1e-4)
+
+
+def test_fullsize_nonnegative_and_unit_norm(cuda_device, video):
+    """All 50 steps from x0 = f: the result is unit-norm and >= 0
+    (Perron-Frobenius; alpha * range(f)^2 <= 1 here), and the Rayleigh
+    quotients never exceed the Gershgorin bound max_i sum_j |M_ij|."""
+    import torch
+    f = video
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p)
+    d = to_dev(f)
+    x = eng.power_iterate(d, d, d, WL.iters)
+    torch.cuda.synchronize()
+    tr = eng.trace()
+    eng.close()
+    xn = x.cpu().numpy()
+    assert abs(np.linalg.norm(xn.astype(np.float64)) - 1) < 1e-5
+    assert xn.min() >= -1e-9
+    gsum = np.prod([oracle.taps(r, s).sum() for r, s in zip(RADII, SIG)])
+    assert np.all(tr["rayleigh"] <= gsum * 1.0001) and len(tr["rayleigh"]) == WL.iters
+
+
+def _rounded_inputs(f, storage):
+    """sp = f^p and f, x0 = f rounded to the storage type (as FP32 values), so
+    the oracle and every run see identical operands."""
+    sp = (f.astype(np.float32) ** np.float32(WL.p)).astype(np.float32)
+    return (oracle.to_storage(sp, storage).astype(np.float32),
+            oracle.to_storage(f, storage).astype(np.float32))
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_fullsize_low_precision_sampled_one_step(cuda_device, video, storage):
+    """BF16/FP16 storage at full size, one step y = M f at sampled voxels vs
+    the oracle fed the same rounded operands."""
+    sp, fr = _rounded_inputs(video, storage)
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p, storage=storage,
+                   flags=sf.SFSEG_S_IS_SP)
+    eng.load_features(to_dev(sp), to_dev(fr))
+    y = eng.apply(to_dev(fr)).cpu().numpy().ravel()
+    eng.close()
+    idx = np.random.default_rng(23).integers(0, fr.size, 4096)
+    ref = oracle.apply_M_at(sp, fr, fr, RADII, SIG, WL.alpha, idx)
+    assert rel_l2(y[idx], ref) < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_fullsize_low_precision_fifty_steps(cuda_device, video, storage):
+    """50 steps with BF16/FP16 storage vs the FP32-storage path on the same
+    rounded operands (the FP32 path is pinned to the oracle above): the
+    storage rounding of the iterates stays within the 1e-3 bar."""
+    import torch
+    sp, fr = _rounded_inputs(video, storage)
+    out = {}
+    for st in ("f32", storage):
+        eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p, storage=st,
+                       flags=sf.SFSEG_S_IS_SP)
+        out[st] = eng.power_iterate(to_dev(sp), to_dev(fr), to_dev(fr), WL.iters).cpu().numpy()
+        eng.close()
+    torch.cuda.synchronize()
+    assert rel_l2(out[storage], out["f32"]) < TOL_LOWP
