@@ -168,10 +168,13 @@ size_t generic_smem_bytes(int rt, int ry, int rx) {
 
 void generic_tile(int* tx, int* ty) { *tx = GT_TX; *ty = GT_TY; }
 
-// The dynamic shared-memory opt-in is set once per context (not during a
-// stream capture); the launch itself only enqueues.
-cudaError_t setup_step_generic(int rt, int ry, int rx) {
-    const int smem = (int)generic_smem_bytes(rt, ry, rx);
+// The dynamic shared-memory opt-in is set at context creation (not during a
+// stream capture); the launch itself only enqueues.  The opt-in is a
+// per-function attribute shared by every context in the process, so it is
+// always set to the size of the largest supported radii: a later context with
+// small radii must not lower the limit another context's launches rely on.
+cudaError_t setup_step_generic(int, int, int) {
+    const int smem = (int)generic_smem_bytes(kMaxRt, kMaxR, kMaxR);
     cudaError_t e = cudaFuncSetAttribute(step_generic_kernel<float>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
