@@ -164,6 +164,27 @@ sfseg_status sfseg_adjoint(sfseg_ctx* ctx, const float* d_gx, float* d_gsp,
  * the last power_iterate/rayleigh/apply: OK, EZERONORM or ENONFINITE. */
 sfseg_status sfseg_sync_status(sfseg_ctx* ctx);
 
+/* Power iteration without any device allocation, for callers that cannot
+ * call cudaMalloc: code running inside a region captured into a larger CUDA
+ * graph, real-time paths with a fixed memory budget (cudaMalloc can stall
+ * every stream and can fail under pressure), plug-ins whose host framework
+ * owns all device memory.  The paper has no counterpart: this is a packaging
+ * of the same computation as sfseg_power_iterate (generic step kernel, exactly
+ * n_iters steps, x0 = d_x in, unit-norm x^K out, FP32 [nf][h][w] device
+ * buffers owned by the caller).  Its workspace is one fixed 32 MiB device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits; volumes needing more (about 2 million voxels in FP32
+ * storage) are rejected with SFSEG_EINVAL before any launch.  All calls share
+ * that array, so calls that overlap on the GPU race: serialise them on one
+ * stream.  The first call on a device looks up the array's address (and the
+ * driver may load the library's device code then): make it before any stream
+ * capture.  d_trace: nullable device array [min(n_iters,1024)][3] receiving
+ * (r_k, rho_k, ||M x^k||).  Device-side statuses (zero norm, non-finite) are
+ * not reported; errors of the call itself are, with sfseg_last_error(NULL). */
+sfseg_status sfseg_power_iterate_noalloc(const sfseg_params* prm, const float* d_s,
+                                         const float* d_f, float* d_x, int32_t n_iters,
+                                         double* d_trace, void* stream);
+
 /* Message of the last failure on ctx (ctx may be NULL: last create failure). */
 const char* sfseg_last_error(const sfseg_ctx* ctx);
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "sfseg_load_features", "sfseg_power_iterate", "sfseg_load_features_batched",
     "sfseg_power_iterate_batched", "sfseg_rayleigh", "sfseg_apply", "sfseg_get_trace",
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
-    "sfseg_launch_count",
+    "sfseg_launch_count", "sfseg_power_iterate_noalloc",
 )
 
 
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "sfseg_last_error": (ctypes.c_char_p, [_vp]),
         "sfseg_status_string": (ctypes.c_char_p, [_i32]),
         "sfseg_launch_count": (ctypes.c_int64, [_vp]),
+        "sfseg_power_iterate_noalloc": (_i32, [P, _vp, _vp, _vp, _i32, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -205,6 +206,14 @@ def sfseg_status_string(st: int) -> str:
 
 def sfseg_launch_count(ctx: int) -> int:
     return int(load_library().sfseg_launch_count(ctx))
+
+
+def sfseg_power_iterate_noalloc(params: sfseg_params, d_s: int, d_f: int, d_x: int,
+                                n_iters: int, d_trace=None, stream: int = 0) -> None:
+    """Allocation-free power iteration (fixed workspace inside the library);
+    for callers that may not call cudaMalloc.  See include/sfseg.h."""
+    _check(load_library().sfseg_power_iterate_noalloc(ctypes.byref(params), d_s, d_f, d_x,
+                                                      n_iters, d_trace, stream))
 
 
 # --------------------------------------------------- torch convenience wrapper

@@ -93,6 +93,11 @@ static sfseg_status validate(const sfseg_params* p) {
     return SFSEG_OK;
 }
 
+namespace sfseg {
+sfseg_status validate_params(const sfseg_params* p) { return validate(p); }
+void set_global_error(const char* msg) { g_create_err = msg ? msg : ""; }
+}  // namespace sfseg
+
 static void free_ctx(sfseg_ctx* c) {
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     c->graphs.clear();

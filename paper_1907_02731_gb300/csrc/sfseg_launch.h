@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "sfseg.h"
 #include "sfseg_common.cuh"
 
 namespace sfseg {
@@ -59,6 +60,12 @@ cudaError_t launch_prep_x(int storage, const PrepXParams& P, int blocks, cudaStr
 cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s);
 cudaError_t launch_set_ptrs(float** dst, float* const* src, int n, cudaStream_t s);
 int prep_x_blocks(long long n);
+
+// ---------------------------------------------------------- host helpers
+// Parameter validation of sfseg_create, and the message slot that
+// sfseg_last_error(NULL) returns (for entry points without a context).
+sfseg_status validate_params(const sfseg_params* p);
+void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- steps
 size_t generic_smem_bytes(int rt, int ry, int rx);
