@@ -191,6 +191,22 @@ const char* sfseg_last_error(const sfseg_ctx* ctx);
 /* Static name of a status code. */
 const char* sfseg_status_string(sfseg_status st);
 
+/* Host-only introspection of the work decomposition of the specialised step
+ * kernel (no device needed).  Units are the output frames of every (video,
+ * 112x12 tile); n_ctas = min(n_sms, units/8) persistent CTAs.  Per video,
+ * while at least n_ctas of its tiles remain, each round gives every CTA one
+ * whole tile (CTA c gets that video's tiles c, c + n_ctas, ...); the units of
+ * every video's last < n_ctas tiles are laid end to end and split into n_ctas
+ * equal contiguous ranges.  dims: [n_videos][3] (nf, h, w).  Writes up
+ * to seg_cap segments as [video, x0, y0, t0, t1) rows into `segments` and up
+ * to cta_cap entries of `cta_begin` (CTA c owns segments [cta_begin[c],
+ * cta_begin[c+1])); either may be NULL.  Returns the number of segments, or
+ * -1 (EINVAL, message in sfseg_last_error(NULL)).  The number of CTAs is the
+ * number of cta_begin entries minus one (at most n_sms). */
+int32_t sfseg_plan_segments(int32_t n_videos, const int32_t* dims, int32_t n_sms,
+                            int32_t* segments, int32_t seg_cap, int32_t* cta_begin,
+                            int32_t cta_cap);
+
 /* Number of kernel launches this context issued so far (for accounting). */
 int64_t sfseg_launch_count(const sfseg_ctx* ctx);
 

@@ -31,7 +31,7 @@ EXPORTS = (
     "sfseg_load_features", "sfseg_power_iterate", "sfseg_load_features_batched",
     "sfseg_power_iterate_batched", "sfseg_rayleigh", "sfseg_apply", "sfseg_get_trace",
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
-    "sfseg_launch_count", "sfseg_power_iterate_noalloc",
+    "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
 )
 
 
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
         "sfseg_status_string": (ctypes.c_char_p, [_i32]),
         "sfseg_launch_count": (ctypes.c_int64, [_vp]),
         "sfseg_power_iterate_noalloc": (_i32, [P, _vp, _vp, _vp, _i32, _vp, _vp]),
+        "sfseg_plan_segments": (_i32, [_i32, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32),
+                                       _i32, ctypes.POINTER(_i32), _i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -214,6 +216,22 @@ def sfseg_power_iterate_noalloc(params: sfseg_params, d_s: int, d_f: int, d_x: i
     for callers that may not call cudaMalloc.  See include/sfseg.h."""
     _check(load_library().sfseg_power_iterate_noalloc(ctypes.byref(params), d_s, d_f, d_x,
                                                       n_iters, d_trace, stream))
+
+
+def sfseg_plan_segments(dims, n_sms: int):
+    """Work decomposition of the specialised kernel (host only): returns
+    (segments [n][5] as (video, x0, y0, t0, t1), cta_begin list)."""
+    flat = (_i32 * (3 * len(dims)))(*[int(v) for d in dims for v in d])
+    L = load_library()
+    n = L.sfseg_plan_segments(len(dims), flat, n_sms, None, 0, None, 0)
+    if n < 0:
+        _check(SFSEG_EINVAL)
+    segs = (_i32 * (5 * n))()
+    cb = (_i32 * (n_sms + 1))(*([-1] * (n_sms + 1)))
+    L.sfseg_plan_segments(len(dims), flat, n_sms, segs, n, cb, n_sms + 1)
+    rows = [tuple(segs[5 * i:5 * i + 5]) for i in range(n)]
+    cta = [c for c in cb if c >= 0]
+    return rows, cta
 
 
 # --------------------------------------------------- torch convenience wrapper

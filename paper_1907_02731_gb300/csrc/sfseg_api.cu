@@ -8,6 +8,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "sfseg.h"
 #include "sfseg_launch.h"
 
@@ -38,6 +41,12 @@ struct sfseg_ctx {
     int trace_cap = 0;
     float** d_out = nullptr;
     int n_items = 0;
+    // specialised kernel: balanced segment lists and TMA descriptors
+    bool fast = false;
+    int n_ctas = 0;
+    int* d_cta_begin = nullptr;
+    int* d_vseg = nullptr;
+    CUtensorMap* d_maps = nullptr;
     std::vector<int> item_begin;
     // host-side
     float gt[2 * kMaxRt + 1], gy[2 * kMaxR + 1], gx[2 * kMaxR + 1];
@@ -103,7 +112,7 @@ static void free_ctx(sfseg_ctx* c) {
     c->graphs.clear();
     void* ptrs[] = {c->sp, c->f, c->xa, c->xb, c->d_geo, c->d_state, c->d_items, c->d_item_begin,
                     c->d_partials, c->d_counters, c->d_prep_partials, c->d_prep_counter, c->d_bad,
-                    c->d_trace, c->d_out};
+                    c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -117,6 +126,127 @@ static void host_taps(int r, double sigma, float* g, double* sum) {
         s += (double)(float)v;
     }
     *sum *= s;
+}
+
+// Work decomposition of the specialised kernel.  Units = output frames of
+// (video, tile) pairs.  n_ctas = min(sms, units / 8).  Per video, while at
+// least n_ctas of its tiles remain, a round gives CTA c one whole tile (all
+// CTAs stream their tiles in step, so the halo rows one CTA loads are still
+// in L2 when its neighbours need them); the units of every video's last
+// < n_ctas tiles are laid end to end and cut into n_ctas equal contiguous
+// ranges.  Outputs: segments
+// ordered by CTA, cta_begin, and per-video segment id lists (vseg /
+// item_begin) for the finalize.
+static void build_segments(const std::vector<VideoGeom>& geo, int sms, std::vector<WorkItem>* items,
+                           std::vector<int>* item_begin, std::vector<int>* cta_begin,
+                           std::vector<int>* vseg) {
+    int tx, ty, nt;
+    fast_tile(&tx, &ty, &nt);
+    struct Tile { int v, x0, y0, nf; };
+    long long U = 0;
+    for (const VideoGeom& g : geo)
+        U += (long long)g.nf * ((g.w + tx - 1) / tx) * ((g.h + ty - 1) / ty);
+    long long n = U / 8;                      // at least ~8 output frames per CTA
+    if (n > sms) n = sms;
+    if (n < 1) n = 1;
+    // whole-tile rounds per video (every tile of a round has the same frame
+    // count, so each round adds the same work to every CTA); leftovers of all
+    // videos go to the even split
+    std::vector<std::vector<WorkItem>> per(n);
+    std::vector<Tile> tiles;   // leftovers
+    for (int v = 0; v < (int)geo.size(); ++v) {
+        const VideoGeom& g = geo[v];
+        std::vector<Tile> tv;
+        for (int y0 = 0; y0 < g.h; y0 += ty)
+            for (int x0 = 0; x0 < g.w; x0 += tx) tv.push_back({v, x0, y0, g.nf});
+        const size_t whole = tv.size() / (size_t)n * (size_t)n;
+        for (size_t k = 0; k < whole; ++k) {
+            WorkItem it{};
+            it.video = v;
+            it.x0 = tv[k].x0;
+            it.y0 = tv[k].y0;
+            it.t0 = 0;
+            it.t1 = g.nf;
+            per[k % n].push_back(it);
+        }
+        tiles.insert(tiles.end(), tv.begin() + whole, tv.end());
+    }
+    long long U2 = 0;
+    for (const Tile& t : tiles) U2 += t.nf;
+    long long pos = 0, cur = 0;
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        const long long end_tile = pos + tiles[k].nf;
+        long long t = pos;
+        while (t < end_tile) {
+            while (cur + 1 < n && U2 * (cur + 1) / n <= t) ++cur;
+            const long long cut = U2 * (cur + 1) / n;
+            const long long e = end_tile < cut ? end_tile : cut;
+            WorkItem it{};
+            it.video = tiles[k].v;
+            it.x0 = tiles[k].x0;
+            it.y0 = tiles[k].y0;
+            it.t0 = (int)(t - pos);
+            it.t1 = (int)(e - pos);
+            per[cur].push_back(it);
+            t = e;
+        }
+        pos = end_tile;
+    }
+    cta_begin->assign(n + 1, 0);
+    for (long long c = 0; c < n; ++c) {
+        (*cta_begin)[c] = (int)items->size();
+        items->insert(items->end(), per[c].begin(), per[c].end());
+    }
+    (*cta_begin)[n] = (int)items->size();
+    vseg->clear();
+    item_begin->clear();
+    for (int v = 0; v < (int)geo.size(); ++v) {
+        item_begin->push_back((int)vseg->size());
+        for (int i = 0; i < (int)items->size(); ++i)
+            if ((*items)[i].video == v) vseg->push_back(i);
+    }
+    item_begin->push_back((int)vseg->size());
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// One 3D tiled descriptor per (video, array): dims (w, h, nf) so the box
+// reads zeros outside the volume, row/plane strides of the pitched layout.
+static const char* encode_maps(sfseg_ctx* c, CUtensorMap* maps) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return "cuTensorMapEncodeTiled unavailable";
+    int bw, bh, xpad;
+    fast_box(c->prm.ry, &bw, &bh, &xpad);
+    const CUtensorMapDataType dt = c->prm.storage == SFSEG_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->prm.storage == SFSEG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                  : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    void* arrays[4] = {c->sp, c->f, c->xa, c->xb};
+    for (int v = 0; v < c->nv; ++v) {
+        const VideoGeom& g = c->geo[v];
+        cuuint64_t gdim[3] = {(cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.nf};
+        cuuint64_t gstr[2] = {(cuuint64_t)g.pitch * c->elt, (cuuint64_t)g.plane * c->elt};
+        cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
+        cuuint32_t est[3] = {1u, 1u, 1u};
+        for (int a = 0; a < 4; ++a) {
+            void* base = (char*)arrays[a] + (size_t)g.off * c->elt;
+            CUresult r = enc(&maps[4 * v + a], dt, 3, base, gdim, gstr, box, est,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed";
+        }
+    }
+    return nullptr;
 }
 
 static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* dims, bool batched,
@@ -137,9 +267,6 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
     c->elt = prm->storage == SFSEG_F32 ? 4 : 2;
     const long long align = 256 / (long long)c->elt;
     long long off = 0;
-    int tx, ty;
-    generic_tile(&tx, &ty);
-    std::vector<WorkItem> items;
     for (int v = 0; v < nv; ++v) {
         VideoGeom g;
         g.nf = dims[3 * v];
@@ -151,19 +278,36 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         g.n = (long long)g.nf * g.h * g.w;
         off += (g.nf * g.plane + align - 1) / align * align;
         c->geo.push_back(g);
-        c->item_begin.push_back((int)items.size());
-        for (int y0 = 0; y0 < g.h; y0 += ty)
-            for (int x0 = 0; x0 < g.w; x0 += tx) {
-                WorkItem it{};
-                it.video = v;
-                it.x0 = x0;
-                it.y0 = y0;
-                it.t0 = 0;
-                it.t1 = g.nf;
-                items.push_back(it);
-            }
     }
-    c->item_begin.push_back((int)items.size());
+    c->fast = !(prm->flags & SFSEG_GENERIC) && fast_available(prm->rt, prm->ry, prm->rx, prm->storage);
+    std::vector<WorkItem> items;
+    std::vector<int> cta_begin, vseg;
+    if (c->fast) {
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+            sms = 1;
+        build_segments(c->geo, sms, &items, &c->item_begin, &cta_begin, &vseg);
+        c->n_ctas = (int)cta_begin.size() - 1;
+    } else {
+        int tx, ty;
+        generic_tile(&tx, &ty);
+        for (int v = 0; v < nv; ++v) {
+            const VideoGeom& g = c->geo[v];
+            c->item_begin.push_back((int)items.size());
+            for (int y0 = 0; y0 < g.h; y0 += ty)
+                for (int x0 = 0; x0 < g.w; x0 += tx) {
+                    WorkItem it{};
+                    it.video = v;
+                    it.x0 = x0;
+                    it.y0 = y0;
+                    it.t0 = 0;
+                    it.t1 = g.nf;
+                    items.push_back(it);
+                }
+        }
+        c->item_begin.push_back((int)items.size());
+    }
     c->total = off;
     c->n_items = (int)items.size();
     c->gsum = 1.0;
@@ -196,6 +340,11 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
     ALLOC(c->d_prep_counter, sizeof(unsigned));
     ALLOC(c->d_bad, sizeof(int));
     ALLOC(c->d_out, sizeof(float*) * nv);
+    if (c->fast) {
+        ALLOC(c->d_cta_begin, sizeof(int) * cta_begin.size());
+        ALLOC(c->d_vseg, sizeof(int) * (vseg.size() + 1));
+        ALLOC(c->d_maps, sizeof(CUtensorMap) * 4 * nv);
+    }
 #undef ALLOC
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemset(c->sp, 0, vol);
@@ -214,6 +363,25 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         e = cudaMemcpy(c->d_item_begin, c->item_begin.data(), sizeof(int) * (nv + 1),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = setup_step_generic(prm->rt, prm->ry, prm->rx);
+    if (e == cudaSuccess && c->fast) {
+        e = setup_step_fast(prm->rt, prm->ry, prm->rx, prm->storage);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->d_cta_begin, cta_begin.data(), sizeof(int) * cta_begin.size(),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !vseg.empty())
+            e = cudaMemcpy(c->d_vseg, vseg.data(), sizeof(int) * vseg.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            std::vector<CUtensorMap> maps(4 * (size_t)nv);
+            const char* why = encode_maps(c, maps.data());
+            if (why) {
+                fail(nullptr, SFSEG_ECUDA, "tensor map: %s", why);
+                free_ctx(c);
+                return SFSEG_ECUDA;
+            }
+            e = cudaMemcpy(c->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                           cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -264,12 +432,17 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store) {
     memcpy(P.gt, c->gt, sizeof c->gt);
     memcpy(P.gy, c->gy, sizeof c->gy);
     memcpy(P.gx, c->gx, sizeof c->gx);
+    P.maps = c->d_maps;
+    P.x_sel = k & 1;
+    P.cta_begin = c->d_cta_begin;
+    P.vseg = c->d_vseg;
     return P;
 }
 
 static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s) {
     StepParams P = step_params(c, k, final_out, store);
     c->launches += 1;
+    if (c->fast) return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
     return launch_step_generic(c->prm.storage, P, c->n_items, s);
 }
 
@@ -597,5 +770,40 @@ const char* sfseg_status_string(sfseg_status st) {
 }
 
 int64_t sfseg_launch_count(const sfseg_ctx* c) { return c ? c->launches : 0; }
+
+int32_t sfseg_plan_segments(int32_t n_videos, const int32_t* dims, int32_t n_sms,
+                            int32_t* segments, int32_t seg_cap, int32_t* cta_begin,
+                            int32_t cta_cap) {
+    if (n_videos < 1 || !dims || n_sms < 1) {
+        fail(nullptr, SFSEG_EINVAL, "plan: bad arguments");
+        return -1;
+    }
+    std::vector<VideoGeom> geo;
+    for (int v = 0; v < n_videos; ++v) {
+        if (dims[3 * v] < 1 || dims[3 * v + 1] < 1 || dims[3 * v + 2] < 1) {
+            fail(nullptr, SFSEG_EINVAL, "plan: video %d has an empty dimension", v);
+            return -1;
+        }
+        VideoGeom g{};
+        g.nf = dims[3 * v];
+        g.h = dims[3 * v + 1];
+        g.w = dims[3 * v + 2];
+        geo.push_back(g);
+    }
+    std::vector<WorkItem> items;
+    std::vector<int> ib, cb, vs;
+    build_segments(geo, n_sms, &items, &ib, &cb, &vs);
+    if (segments)
+        for (int i = 0; i < (int)items.size() && i < seg_cap; ++i) {
+            segments[5 * i + 0] = items[i].video;
+            segments[5 * i + 1] = items[i].x0;
+            segments[5 * i + 2] = items[i].y0;
+            segments[5 * i + 3] = items[i].t0;
+            segments[5 * i + 4] = items[i].t1;
+        }
+    if (cta_begin)
+        for (int i = 0; i < (int)cb.size() && i < cta_cap; ++i) cta_begin[i] = cb[i];
+    return (int32_t)items.size();
+}
 
 }  // extern "C"

@@ -56,7 +56,8 @@ struct StepParams {
     const VideoGeom* geo;
     VState* state;
     const WorkItem* items;
-    const int* item_begin;      // [n_videos + 1]: items of video v are [b[v], b[v+1])
+    const int* item_begin;      // [n_videos + 1]: video v's items are vseg[b[v] .. b[v+1])
+    const int* vseg;            // item ids grouped by video (null: identity)
     double* partials;           // [n_items][kRed]
     unsigned* counters;         // [n_videos]
     double* trace;              // [n_videos][trace_cap][3]: r_k, rho_k, ||M x_hat||
@@ -67,6 +68,10 @@ struct StepParams {
     float gt[2 * kMaxRt + 1];
     float gy[2 * kMaxR + 1];
     float gx[2 * kMaxR + 1];
+    // specialised kernel only
+    const void* maps;           // [n_videos][4] CUtensorMap: sp, f, x_a, x_b (global memory)
+    int x_sel;                  // 0: the input iterate is x_a, 1: x_b
+    const int* cta_begin;       // [n_ctas + 1]: segments of CTA c are [cta_begin[c], cta_begin[c+1])
 };
 
 // ---------------------------------------------------------------- storage
@@ -170,7 +175,10 @@ __device__ inline void arrive_and_finalize(const StepParams& P, int v, double* s
     const int b = P.item_begin[v], e = P.item_begin[v + 1];
     double acc[kRed] = {0.0, 0.0, 0.0, 0.0};
     for (int i = b + (int)threadIdx.x; i < e; i += blockDim.x)
-        for (int c = 0; c < kRed; ++c) acc[c] += __ldcg(&P.partials[(long long)i * kRed + c]);
+        for (int c = 0; c < kRed; ++c) {
+            const long long id = P.vseg ? P.vseg[i] : i;
+            acc[c] += __ldcg(&P.partials[id * kRed + c]);
+        }
     // tree over threads in shared memory (fixed order)
     double* red = sh;   // blockDim * kRed doubles
     for (int c = 0; c < kRed; ++c) red[c * blockDim.x + threadIdx.x] = acc[c];

@@ -73,4 +73,12 @@ void generic_tile(int* tx, int* ty);
 cudaError_t setup_step_generic(int rt, int ry, int rx);
 cudaError_t launch_step_generic(int storage, const StepParams& P, int n_items, cudaStream_t s);
 
+// Specialised kernel for radii (2,5,5), (3,3,3), (2,4,4): 128 x 16 tiles,
+// persistent CTAs of 512 threads over balanced segment lists, TMA loads.
+bool fast_available(int rt, int ry, int rx, int storage);
+void fast_tile(int* tx, int* ty, int* threads);
+void fast_box(int ry, int* box_w, int* box_h, int* x_pad);   // TMA box of one stage array
+cudaError_t setup_step_fast(int rt, int ry, int rx, int storage);
+cudaError_t launch_step_fast(int storage, const StepParams& P, int n_ctas, cudaStream_t s);
+
 }  // namespace sfseg
