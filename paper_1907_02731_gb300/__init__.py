@@ -314,6 +314,16 @@ class SFSeg:
         sfseg_apply(self.ctx, x.data_ptr(), _dev_f32(y, "y").data_ptr(), _stream_handle())
         return y
 
+    def adjoint(self, gx):
+        """(dL/dsp, dL/df, dL/dx0) of the last recorded power_iterate, given
+        dL/dx^K (the context must be created with SFSEG_RECORD)."""
+        import torch
+        gx = _dev_f32(gx, "gx")
+        gsp, gf, gx0 = (torch.empty_like(gx) for _ in range(3))
+        sfseg_adjoint(self.ctx, gx.data_ptr(), gsp.data_ptr(), gf.data_ptr(), gx0.data_ptr(),
+                      _stream_handle())
+        return gsp, gf, gx0
+
     def trace(self, video: int = 0):
         return sfseg_get_trace(self.ctx, video)
 

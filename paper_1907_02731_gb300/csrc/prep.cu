@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
         else if (!(xx > 0.0)) { st.status = 4; st.done = 1; st.scale = 0.0; }
         else st.scale = 1.0 / sqrt(xx);
     }
+    if (P.rec_scale0) *P.rec_scale0 = st.scale;
     P.state[P.video] = st;
 }
 

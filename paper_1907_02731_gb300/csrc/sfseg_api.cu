@@ -47,6 +47,24 @@ struct sfseg_ctx {
     int* d_cta_begin = nullptr;
     int* d_vseg = nullptr;
     CUtensorMap* d_maps = nullptr;
+    // generic tile plan (always built): the adjoint and its forward recompute
+    WorkItem* d_gitems = nullptr;
+    int* d_gitem_begin = nullptr;
+    double* d_gpartials = nullptr;
+    int g_n_items = 0;
+    // forward record and adjoint workspace (allocated on first use)
+    int rec_cap = 0;            // steps the record arrays hold
+    double* d_rec = nullptr;    // [3][rec_cap + 1]: scale, gain, ny
+    double* d_rrec = nullptr;   // the same for the backward's recompute
+    int ckpt_cap = 0;
+    void* d_ckpt = nullptr;     // [ckpt_cap] volumes: x^{j C} (and x^K last)
+    void* d_adj = nullptr;      // [C + 4] volumes: recompute ring, g ping-pong, dsp, df
+    int adj_cap = 0;
+    double* d_adjc = nullptr;   // [2] dot products
+    double* d_adj_partials = nullptr;
+    unsigned* d_adj_counter = nullptr;
+    bool recorded = false;
+    int rec_K = 0;
     std::vector<int> item_begin;
     // host-side
     float gt[2 * kMaxRt + 1], gy[2 * kMaxR + 1], gx[2 * kMaxR + 1];
@@ -112,7 +130,9 @@ static void free_ctx(sfseg_ctx* c) {
     c->graphs.clear();
     void* ptrs[] = {c->sp, c->f, c->xa, c->xb, c->d_geo, c->d_state, c->d_items, c->d_item_begin,
                     c->d_partials, c->d_counters, c->d_prep_partials, c->d_prep_counter, c->d_bad,
-                    c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps};
+                    c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps,
+                    c->d_gitems, c->d_gitem_begin, c->d_gpartials, c->d_rec, c->d_rrec,
+                    c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -289,7 +309,30 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
             sms = 1;
         build_segments(c->geo, sms, &items, &c->item_begin, &cta_begin, &vseg);
         c->n_ctas = (int)cta_begin.size() - 1;
-    } else {
+    }
+    std::vector<WorkItem> gitems;
+    std::vector<int> gitem_begin;
+    {
+        int tx, ty;
+        generic_tile(&tx, &ty);
+        for (int v = 0; v < nv; ++v) {
+            const VideoGeom& g = c->geo[v];
+            gitem_begin.push_back((int)gitems.size());
+            for (int y0 = 0; y0 < g.h; y0 += ty)
+                for (int x0 = 0; x0 < g.w; x0 += tx) {
+                    WorkItem it{};
+                    it.video = v;
+                    it.x0 = x0;
+                    it.y0 = y0;
+                    it.t0 = 0;
+                    it.t1 = g.nf;
+                    gitems.push_back(it);
+                }
+        }
+        gitem_begin.push_back((int)gitems.size());
+        c->g_n_items = (int)gitems.size();
+    }
+    if (!c->fast) {
         int tx, ty;
         generic_tile(&tx, &ty);
         for (int v = 0; v < nv; ++v) {
@@ -340,6 +383,9 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
     ALLOC(c->d_prep_counter, sizeof(unsigned));
     ALLOC(c->d_bad, sizeof(int));
     ALLOC(c->d_out, sizeof(float*) * nv);
+    ALLOC(c->d_gitems, sizeof(WorkItem) * gitems.size());
+    ALLOC(c->d_gitem_begin, sizeof(int) * gitem_begin.size());
+    ALLOC(c->d_gpartials, sizeof(double) * kRed * gitems.size());
     if (c->fast) {
         ALLOC(c->d_cta_begin, sizeof(int) * cta_begin.size());
         ALLOC(c->d_vseg, sizeof(int) * (vseg.size() + 1));
@@ -361,6 +407,11 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         e = cudaMemcpy(c->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_item_begin, c->item_begin.data(), sizeof(int) * (nv + 1),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_gitems, gitems.data(), sizeof(WorkItem) * gitems.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_gitem_begin, gitem_begin.data(), sizeof(int) * gitem_begin.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = setup_step_generic(prm->rt, prm->ry, prm->rx);
     if (e == cudaSuccess && c->fast) {
@@ -409,7 +460,8 @@ static sfseg_status ensure_trace(sfseg_ctx* c, int K) {
     return SFSEG_OK;
 }
 
-static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store) {
+static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
+                              bool record = false) {
     StepParams P{};
     P.x_in = (k & 1) ? c->xb : c->xa;
     P.z_out = (store && !final_out) ? ((k & 1) ? c->xa : c->xb) : nullptr;
@@ -436,11 +488,17 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store) {
     P.x_sel = k & 1;
     P.cta_begin = c->d_cta_begin;
     P.vseg = c->d_vseg;
+    if (record && c->d_rec) {
+        P.rec.scale = c->d_rec;
+        P.rec.gain = c->d_rec + (c->rec_cap + 1);
+        P.rec.ny = c->d_rec + 2 * (c->rec_cap + 1);
+    }
     return P;
 }
 
-static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s) {
-    StepParams P = step_params(c, k, final_out, store);
+static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s,
+                               bool record = false) {
+    StepParams P = step_params(c, k, final_out, store, record);
     c->launches += 1;
     if (c->fast) return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
     return launch_step_generic(c->prm.storage, P, c->n_items, s);
@@ -508,8 +566,10 @@ static sfseg_status load_features_impl(sfseg_ctx* c, const float* const* d_s, co
     return SFSEG_OK;
 }
 
-static sfseg_status prep_x(sfseg_ctx* c, int v, const float* d_x, bool raw, double tol, cudaStream_t s) {
+static sfseg_status prep_x(sfseg_ctx* c, int v, const float* d_x, bool raw, double tol, cudaStream_t s,
+                           double* rec_scale0 = nullptr) {
     PrepXParams P{};
+    P.rec_scale0 = rec_scale0;
     P.x = d_x;
     P.x_out = c->xa;
     P.g = c->geo[v];
@@ -538,6 +598,70 @@ static sfseg_status device_status(sfseg_ctx* c, cudaStream_t s, std::vector<VSta
     return SFSEG_OK;
 }
 
+static size_t vol_bytes(const sfseg_ctx* c) { return (size_t)c->total * c->elt; }
+
+static sfseg_status ensure_record(sfseg_ctx* c, int K) {
+    const int C = c->prm.ckpt_every > 0 ? c->prm.ckpt_every : 8;
+    const int nck = (K + C - 1) / C + 1;
+    if (K > c->rec_cap) {
+        CUDA_OR(c, cudaDeviceSynchronize());
+        if (c->d_rec) cudaFree(c->d_rec);
+        if (c->d_rrec) cudaFree(c->d_rrec);
+        c->d_rec = c->d_rrec = nullptr;
+        c->rec_cap = 0;
+        CUDA_OR(c, cudaMalloc((void**)&c->d_rec, sizeof(double) * 3 * (K + 1)));
+        CUDA_OR(c, cudaMalloc((void**)&c->d_rrec, sizeof(double) * 3 * (K + 1)));
+        c->rec_cap = K;
+    }
+    if (nck > c->ckpt_cap) {
+        CUDA_OR(c, cudaDeviceSynchronize());
+        if (c->d_ckpt) cudaFree(c->d_ckpt);
+        c->d_ckpt = nullptr;
+        c->ckpt_cap = 0;
+        CUDA_OR(c, cudaMalloc(&c->d_ckpt, vol_bytes(c) * nck));
+        c->ckpt_cap = nck;
+    }
+    return SFSEG_OK;
+}
+
+static void* ckpt_ptr(sfseg_ctx* c, int j) { return (char*)c->d_ckpt + vol_bytes(c) * (size_t)j; }
+
+// Forward pass that keeps what the adjoint needs: the scale, gain and norm
+// of every step, and the stored iterate every C steps (and the last one).
+static sfseg_status iterate_record(sfseg_ctx* c, const float* d_x_in, float* d_x, int K,
+                                   cudaStream_t s) {
+    const int C = c->prm.ckpt_every > 0 ? c->prm.ckpt_every : 8;
+    sfseg_status st = ensure_record(c, K > 0 ? K : 1);
+    if (st != SFSEG_OK) return st;
+    c->recorded = false;
+    st = prep_x(c, 0, d_x_in, false, 0.0, s, c->d_rec);
+    if (st != SFSEG_OK) return st;
+    const size_t vb = vol_bytes(c);
+    CUDA_OR(c, cudaMemcpyAsync(ckpt_ptr(c, 0), c->xa, vb, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < K; ++k) {
+        CUDA_OR(c, launch_step(c, k, false, true, s, true));
+        const int k1 = k + 1;
+        if (k1 % C == 0 || k1 == K) {
+            const void* src = (k1 & 1) ? c->xb : c->xa;
+            CUDA_OR(c, cudaMemcpyAsync(ckpt_ptr(c, (k1 + C - 1) / C), src, vb, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    FinishParams F{};
+    F.out = d_x;
+    F.buf0 = c->xa;
+    F.buf1 = c->xb;
+    F.g = c->geo[0];
+    F.state = c->d_state;
+    F.video = 0;
+    F.final_iter = -1;
+    CUDA_OR(c, launch_finish(c->prm.storage, F, s));
+    c->launches += 1;
+    c->last_stream = s;
+    c->recorded = true;
+    c->rec_K = K;
+    return SFSEG_OK;
+}
+
 static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float* const* d_x,
                                  int K, double tol, int32_t* iters_done, cudaStream_t s) {
     if (K < 0) return fail(c, SFSEG_EINVAL, "n_iters must be >= 0");
@@ -547,6 +671,19 @@ static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float
         if (!d_x[v]) return fail(c, SFSEG_EINVAL, "video %d: NULL x pointer", v);
     sfseg_status st = ensure_trace(c, K > 0 ? K : 1);
     if (st != SFSEG_OK) return st;
+    if (c->prm.flags & SFSEG_RECORD) {
+        if (c->nv != 1 || c->prm.storage != SFSEG_F32 || tol != 0.0 || c->prm.nchan != 1)
+            return fail(c, SFSEG_EUNSUPPORTED,
+                        "recording for the adjoint needs one video, FP32 storage, one channel, tol = 0");
+        st = iterate_record(c, d_x_in[0], d_x[0], K, s);
+        if (st == SFSEG_OK && iters_done) {
+            std::vector<VState> vs;
+            st = device_status(c, s, &vs);
+            *iters_done = vs[0].iter;
+        }
+        return st;
+    }
+    c->recorded = false;
     for (int v = 0; v < c->nv; ++v) {
         st = prep_x(c, v, d_x_in[v], false, tol, s);
         if (st != SFSEG_OK) return st;
@@ -740,9 +877,111 @@ int32_t sfseg_get_trace(sfseg_ctx* c, int32_t video, double* rayleigh, double* r
     return n;
 }
 
-sfseg_status sfseg_adjoint(sfseg_ctx* c, const float*, float*, float*, float*, void*) {
+sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float* d_gf,
+                           float* d_gx0, void* stream) {
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
-    return fail(c, SFSEG_EUNSUPPORTED, "adjoint is not built yet");
+    if (!d_gx) return fail(c, SFSEG_EINVAL, "d_gx is NULL");
+    if (!c->recorded) return fail(c, SFSEG_ESTATE, "no recorded forward (create with SFSEG_RECORD)");
+    if (c->rec_K < 1) return fail(c, SFSEG_EUNSUPPORTED, "the recorded forward has no step");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = c->rec_K;
+    const int C = c->prm.ckpt_every > 0 ? c->prm.ckpt_every : 8;
+    const int nseg = (K + C - 1) / C;
+    const VideoGeom& g = c->geo[0];
+    const size_t vb = vol_bytes(c);
+    if (setup_adjoint(c->prm.rt, c->prm.ry, c->prm.rx) != cudaSuccess)
+        return fail(c, SFSEG_EUNSUPPORTED, "radii too large for the adjoint tile");
+    if (c->adj_cap < C + 4) {
+        CUDA_OR(c, cudaDeviceSynchronize());
+        if (c->d_adj) cudaFree(c->d_adj);
+        c->d_adj = nullptr;
+        c->adj_cap = 0;
+        CUDA_OR(c, cudaMalloc(&c->d_adj, vb * (C + 4)));
+        c->adj_cap = C + 4;
+    }
+    if (!c->d_adjc) {
+        CUDA_OR(c, cudaMalloc((void**)&c->d_adjc, sizeof(double) * 2));
+        CUDA_OR(c, cudaMalloc((void**)&c->d_adj_partials, sizeof(double) * c->g_n_items));
+        CUDA_OR(c, cudaMalloc((void**)&c->d_adj_counter, sizeof(unsigned)));
+        CUDA_OR(c, cudaMemset(c->d_adj_counter, 0, sizeof(unsigned)));
+    }
+    auto vol = [&](int j) { return (float*)((char*)c->d_adj + vb * (size_t)j); };
+    float* gb[2] = {vol(C), vol(C + 1)};
+    float* dsp = vol(C + 2);
+    float* df = vol(C + 3);
+    const double* rscale = c->d_rec;
+    const double* rgain = c->d_rec + (c->rec_cap + 1);
+    const double* rny = c->d_rec + 2 * (c->rec_cap + 1);
+    double* qscale = c->d_rrec;   // scales of the recomputed iterates
+    CUDA_OR(c, cudaMemsetAsync(c->d_adj, 0, vb * (C + 4), s));
+    CUDA_OR(c, launch_pitch_copy(d_gx, gb[0], g, 1, nullptr, s));
+    CUDA_OR(c, launch_dot((const float*)ckpt_ptr(c, nseg), rscale + K, gb[0], g, c->d_prep_partials,
+                          c->d_prep_counter, c->d_adjc, prep_x_blocks(g.n), s));
+    c->launches += 2;
+    int cur = 0, cpar = 0;
+    for (int m = nseg - 1; m >= 0; --m) {
+        const int k0 = m * C, k1 = (k0 + C < K) ? k0 + C : K;
+        // recompute x^{k0+1} .. x^{k1-1} from the checkpoint with the generic step
+        if (k1 - k0 > 1) {
+            CUDA_OR(c, launch_set_state(c->d_state, rscale + k0, rgain + k0, k0, s));
+            c->launches += 1;
+            for (int k = k0; k < k1 - 1; ++k) {
+                StepParams P = step_params(c, 0, false, true);
+                P.x_in = (k == k0) ? ckpt_ptr(c, m) : (void*)vol(k - k0);
+                P.z_out = vol(k - k0 + 1);
+                P.items = c->d_gitems;
+                P.item_begin = c->d_gitem_begin;
+                P.vseg = nullptr;
+                P.partials = c->d_gpartials;
+                P.n_items = c->g_n_items;
+                P.trace = nullptr;
+                P.trace_cap = 0;
+                P.rec.scale = qscale;
+                P.rec.gain = qscale + (c->rec_cap + 1);
+                P.rec.ny = qscale + 2 * (c->rec_cap + 1);
+                CUDA_OR(c, launch_step_generic(c->prm.storage, P, c->g_n_items, s));
+                c->launches += 1;
+            }
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            AdjParams A{};
+            A.g_in = gb[cur];
+            A.g_out = gb[1 - cur];
+            A.x_next = (k + 1 == k1) ? (const float*)ckpt_ptr(c, m + 1) : vol(k + 1 - k0);
+            A.s_next = (k + 1 == k1) ? rscale + k1 : qscale + k + 1;
+            A.x_cur = (k == k0) ? (const float*)ckpt_ptr(c, m) : vol(k - k0);
+            A.s_cur = (k == k0) ? rscale + k0 : qscale + k;
+            A.ny = rny + k;
+            A.c_in = c->d_adjc + cpar;
+            A.c_out = c->d_adjc + (1 - cpar);
+            A.sp = (const float*)c->sp;
+            A.f = (const float*)c->f;
+            A.dsp = dsp;
+            A.df = df;
+            A.geo = c->d_geo;
+            A.items = c->d_gitems;
+            A.partials = c->d_adj_partials;
+            A.counter = c->d_adj_counter;
+            A.alpha = (float)c->prm.alpha;
+            A.rt = c->prm.rt;
+            A.ry = c->prm.ry;
+            A.rx = c->prm.rx;
+            memcpy(A.gt, c->gt, sizeof c->gt);
+            memcpy(A.gy, c->gy, sizeof c->gy);
+            memcpy(A.gx, c->gx, sizeof c->gx);
+            CUDA_OR(c, launch_adjoint(A, c->g_n_items, s));
+            c->launches += 1;
+            cur = 1 - cur;
+            cpar = 1 - cpar;
+        }
+    }
+    // dL/dx0 = g_0 / ||x0|| (x^0 was the normalised x0); dL/dsp, dL/df
+    if (d_gx0) CUDA_OR(c, launch_pitch_copy(gb[cur], d_gx0, g, 0, rscale + 0, s));
+    if (d_gsp) CUDA_OR(c, launch_pitch_copy(dsp, d_gsp, g, 0, nullptr, s));
+    if (d_gf) CUDA_OR(c, launch_pitch_copy(df, d_gf, g, 0, nullptr, s));
+    c->launches += 3;
+    c->last_stream = s;
+    return SFSEG_OK;
 }
 
 sfseg_status sfseg_sync_status(sfseg_ctx* c) {

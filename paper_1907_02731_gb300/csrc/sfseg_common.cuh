@@ -20,6 +20,16 @@ namespace sfseg {
 constexpr int kMaxR = 16;       // largest spatial radius
 constexpr int kMaxRt = 8;       // largest temporal radius
 constexpr int kRed = 4;         // reductions per step: z.z, xh.z, xh.xh, |z - s xh|^2
+constexpr int kMaxDynSmem = 232448;   // dynamic shared memory per block (227 KB)
+
+// Per-step record of the forward pass for the adjoint (per video, nullable):
+// scale[k] turns the stored iterate of step k into the unit-norm x^k (k = 0..K),
+// gain[k] is the gain step k stored with, ny[k] = ||M x^k|| with unit-norm x^k.
+struct Record {
+    double* scale;
+    double* gain;
+    double* ny;
+};
 
 struct VideoGeom {
     int nf, h, w, pitch;        // pitch in elements
@@ -72,6 +82,7 @@ struct StepParams {
     const void* maps;           // [n_videos][4] CUtensorMap: sp, f, x_a, x_b (global memory)
     int x_sel;                  // 0: the input iterate is x_a, 1: x_b
     const int* cta_begin;       // [n_ctas + 1]: segments of CTA c are [cta_begin[c], cta_begin[c+1])
+    Record rec;                 // forward record (single video), or all null
 };
 
 // ---------------------------------------------------------------- storage
@@ -124,7 +135,7 @@ __device__ __forceinline__ void block_sum_lane0(double (&acc)[kRed], double* sh)
 // from the FP64 sums S = (z.z, xh.z, xh.xh, |z - shift xh|^2) of video v.
 // Runs in one thread.
 __device__ inline void finish_step(VState* st, double* trace_row, const double (&S)[kRed],
-                                   long long n_vox) {
+                                   long long n_vox, const Record* rec = nullptr) {
     const double zz = S[0], xz = S[1], xx = S[2], dd = S[3];
     const double gain = st->gain, sig = st->shift;
     if (!(isfinite(zz) && isfinite(xz) && isfinite(xx) && isfinite(dd))) {
@@ -150,6 +161,11 @@ __device__ inline void finish_step(VState* st, double* trace_row, const double (
         trace_row[2] = ny * st->in_norm;        // ||M x^k|| at the caller's scale of x^k
     }
     st->in_norm = 1.0;
+    if (rec && rec->scale) {
+        rec->gain[st->iter] = gain;
+        rec->ny[st->iter] = ny;
+        rec->scale[st->iter + 1] = 1.0 / sqrt(zz);
+    }
     st->scale = 1.0 / sqrt(zz);
     const double target = sqrt((double)n_vox) * sqrt(xx) / ny;
     st->gain = exp2(rint(log2(target)));
@@ -195,7 +211,7 @@ __device__ inline void arrive_and_finalize(const StepParams& P, int v, double* s
         VState* st = P.state + v;
         const int k = st->iter;
         double* row = (k < P.trace_cap) ? P.trace + ((long long)v * P.trace_cap + k) * 3 : nullptr;
-        finish_step(st, row, S, P.geo[v].n);
+        finish_step(st, row, S, P.geo[v].n, &P.rec);
         P.counters[v] = 0u;
     }
 }

@@ -35,6 +35,7 @@ struct PrepXParams {
     VState* state;
     double* partials;           // [gridDim.x]
     unsigned* counter;
+    double* rec_scale0;         // nullable: receives the scale of x^0 (forward record)
 };
 
 // Up to kMax device pointers passed by value to a tiny kernel that writes
@@ -60,6 +61,42 @@ cudaError_t launch_prep_x(int storage, const PrepXParams& P, int blocks, cudaStr
 cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s);
 cudaError_t launch_set_ptrs(float** dst, float* const* src, int n, cudaStream_t s);
 int prep_x_blocks(long long n);
+
+// --------------------------------------------------------------- adjoint
+struct AdjParams {
+    const float* g_in;          // g_{k+1} = dL/dx^{k+1}, pitched FP32
+    float* g_out;               // g_k, pitched FP32
+    const float* x_next;        // stored x^{k+1} (FP32), unit norm after * s_next
+    const float* x_cur;         // stored x^k (FP32), unit norm after * s_cur
+    const float* sp;            // internal FP32 sp
+    const float* f;             // internal FP32 f
+    float* dsp;                 // pitched FP32 accumulators (+=)
+    float* df;
+    const VideoGeom* geo;
+    const double* s_next;       // device scalars
+    const double* s_cur;
+    const double* ny;           // ||M x^k||, unit-norm x^k
+    const double* c_in;         // x^{k+1} . g_{k+1}
+    double* c_out;              // receives x^k . g_k
+    const WorkItem* items;      // generic 32 x 16 tiles over all frames (one per CTA)
+    double* partials;           // [n_items]
+    unsigned* counter;
+    float alpha;
+    int rt, ry, rx;
+    float gt[2 * kMaxRt + 1];
+    float gy[2 * kMaxR + 1];
+    float gx[2 * kMaxR + 1];
+};
+
+size_t adjoint_smem_bytes(int rt, int ry, int rx);
+cudaError_t setup_adjoint(int rt, int ry, int rx);
+cudaError_t launch_adjoint(const AdjParams& P, int n_items, cudaStream_t s);
+cudaError_t launch_dot(const float* x, const double* scale_x, const float* gv, const VideoGeom& g,
+                       double* partials, unsigned* counter, double* out, int blocks, cudaStream_t s);
+cudaError_t launch_pitch_copy(const float* src, float* dst, const VideoGeom& g, int to_pitched,
+                              const double* scale, cudaStream_t s);
+cudaError_t launch_set_state(VState* st, const double* scale, const double* gain, int iter,
+                             cudaStream_t s);
 
 // ---------------------------------------------------------- host helpers
 // Parameter validation of sfseg_create, and the message slot that
