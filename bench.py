@@ -152,12 +152,142 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
-def workload_config(wl, storage):
-    return {"workload": wl.name, "frames": wl.nf, "h": wl.h, "w": wl.w,
-            "kernel": f"{2 * wl.rx + 1}x{2 * wl.ry + 1}x{2 * wl.rt + 1}",
-            "sigma_xy": wl.sigma_xy, "sigma_t": wl.sigma_t, "alpha": wl.alpha, "p": wl.p,
-            "iters_per_step": wl.iters, "storage": storage, "x0": "f",
-            "l2": "operands larger than L2 (3 volumes of %.0f MB)" % (wl.n * 4 / 1e6)}
+def workload_config(wl, storage, prob=None):
+    cfg = {"workload": wl.name, "frames": wl.nf, "h": wl.h, "w": wl.w,
+           "kernel": f"{2 * wl.rx + 1}x{2 * wl.ry + 1}x{2 * wl.rt + 1}",
+           "sigma_xy": wl.sigma_xy, "sigma_t": wl.sigma_t, "alpha": wl.alpha, "p": wl.p,
+           "iters_per_step": wl.iters, "storage": storage, "x0": "f",
+           "l2": "operands larger than L2 (3 volumes of %.0f MB)" % (wl.n * 4 / 1e6)}
+    if prob is not None and hasattr(prob, "dims"):
+        cfg.update({"frames": None, "h": None, "w": None, "videos": len(prob.dims),
+                    "voxels": prob.n, "l2": "operands larger than L2 (%.0f MB per volume set)"
+                    % (prob.n * 4 / 1e6)})
+    if wl.name.startswith("grad"):
+        cfg["step"] = "recorded forward + adjoint (checkpoints every 8)"
+    return cfg
+
+
+class SingleVideo:
+    """One seeded video of a named workload (FP32 / BF16 / FP16 storage)."""
+
+    def __init__(self, wl, storage, rank, dev, sf, inputs):
+        import torch
+        self.wl, self.K, self.n = wl, wl.iters, wl.n
+        self.f_np, _ = inputs.make_video(wl.nf, wl.h, wl.w, inputs.config_seed(wl.config, rank),
+                                         wl.n_distractors)
+        self.f = torch.from_numpy(self.f_np).to(dev)
+        self.x = torch.empty_like(self.f)
+        self.eng = sf.SFSeg((wl.nf, wl.h, wl.w), radii=(wl.rt, wl.ry, wl.rx),
+                            sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
+                            storage=storage)
+        self.f_host = torch.from_numpy(self.f_np).pin_memory()
+        self.out_host = torch.empty_like(self.f_host).pin_memory()
+        self.f_dev = torch.empty_like(self.f)
+        self.h2d = self.d2h = int(self.f_host.numel() * 4)
+
+    def step(self, iters):
+        self.x.copy_(self.f)                                       # x0 = f
+        self.eng.power_iterate(self.f, self.f, self.x, iters, out=self.x)
+
+    def e2e_step(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.x.copy_(self.f_dev)
+        self.eng.power_iterate(self.f_dev, self.f_dev, self.x, self.K, out=self.x)
+        self.out_host.copy_(self.x, non_blocking=True)
+
+    def check(self):
+        import torch
+        tr = self.eng.trace()
+        return {"x_norm": float(torch.linalg.vector_norm(self.x.double())),
+                "rayleigh_last": float(tr["rayleigh"][-1]),
+                "residual_last": float(tr["residual"][-1])}
+
+
+class Batch:
+    """The uneven batch: 24 seeded videos, frames U{20..120}, resolutions from
+    {320x240, 480x360, 640x360, 854x480}, 9x9x5 Gaussian, all in one launch
+    per power step (replayed as a CUDA graph)."""
+
+    def __init__(self, wl, storage, rank, dev, sf, inputs):
+        import torch
+        self.K = wl.iters
+        dims = inputs.batch_layout()
+        self.dims = dims
+        self.n = sum(nf * h * w for nf, h, w in dims)
+        self.f_np = [inputs.make_video(nf, h, w, inputs.config_seed(inputs.BATCH_CONFIG, 100 * rank + i), 2)[0]
+                     for i, (nf, h, w) in enumerate(dims)]
+        self.fs = [torch.from_numpy(a).to(dev) for a in self.f_np]
+        self.xs = [torch.empty_like(t) for t in self.fs]
+        self.eng = sf.SFSeg(batch_shapes=dims, radii=(wl.rt, wl.ry, wl.rx),
+                            sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
+                            storage=storage)
+        self.f_host = [torch.from_numpy(a).pin_memory() for a in self.f_np]
+        self.out_host = [torch.empty_like(t).pin_memory() for t in self.f_host]
+        self.f_dev = [torch.empty_like(t) for t in self.fs]
+        self.h2d = self.d2h = int(sum(t.numel() for t in self.f_host) * 4)
+
+    def step(self, iters):
+        for x, f in zip(self.xs, self.fs):
+            x.copy_(f)
+        self.eng.power_iterate_batched(self.fs, self.fs, self.xs, iters)
+
+    def e2e_step(self):
+        for fd, fh, x in zip(self.f_dev, self.f_host, self.xs):
+            fd.copy_(fh, non_blocking=True)
+            x.copy_(fd)
+        self.eng.power_iterate_batched(self.f_dev, self.f_dev, self.xs, self.K)
+        for oh, x in zip(self.out_host, self.xs):
+            oh.copy_(x, non_blocking=True)
+
+    def check(self):
+        import torch
+        return {"x_norm_min": min(float(torch.linalg.vector_norm(x.double())) for x in self.xs),
+                "videos": len(self.xs), "voxels": self.n}
+
+
+class Grad:
+    """Differentiable form: 854x480x48, 40 recorded power steps, then the
+    adjoint of L = sum(target * x^K) w.r.t. sp, f and x0 (checkpoints every 8
+    steps).  One bench step = forward + backward."""
+
+    def __init__(self, wl, storage, rank, dev, sf, inputs):
+        import torch
+        from paper_1907_02731_gb300.autograd import make_engine
+        self.K, self.n = wl.iters, wl.n
+        f_np, mask = inputs.make_video(wl.nf, wl.h, wl.w, inputs.config_seed(wl.config, rank),
+                                       wl.n_distractors)
+        self.f_np = f_np
+        self.f = torch.from_numpy(f_np).to(dev)
+        self.target = torch.from_numpy(mask.astype("float32")).to(dev)
+        self.x = torch.empty_like(self.f)
+        self.eng = make_engine((wl.nf, wl.h, wl.w), radii=(wl.rt, wl.ry, wl.rx),
+                               sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p)
+        self.f_host = torch.from_numpy(f_np).pin_memory()
+        self.out_host = torch.empty_like(self.f_host).pin_memory()
+        self.f_dev = torch.empty_like(self.f)
+        self.h2d = int(self.f_host.numel() * 4)
+        self.d2h = 3 * self.h2d
+
+    def step(self, iters):
+        self.x.copy_(self.f)
+        self.eng.power_iterate(self.f, self.f, self.x, max(iters, 1), out=self.x)
+        if iters > 0:
+            self.grads = self.eng.adjoint(self.target)
+
+    def e2e_step(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.x.copy_(self.f_dev)
+        self.eng.power_iterate(self.f_dev, self.f_dev, self.x, self.K, out=self.x)
+        gsp, gf, gx0 = self.eng.adjoint(self.target)
+        for g in (gsp, gf, gx0):
+            self.out_host.copy_(g, non_blocking=True)
+
+    def check(self):
+        import torch
+        gsp, gf, gx0 = self.grads
+        return {"grad_x0_dot_x0_rel": float((gx0.double() * self.f.double()).sum()
+                                            / (gx0.norm() * self.f.norm())),
+                "grad_f_norm": float(gf.norm())}
 
 
 def run_ours(args, wl):
@@ -172,19 +302,9 @@ def run_ours(args, wl):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-
-    f_np, _ = inputs.make_video(wl.nf, wl.h, wl.w, inputs.config_seed(wl.config, rank),
-                                wl.n_distractors)
-    f = torch.from_numpy(f_np).to(dev)
-    x = torch.empty_like(f)
-    eng = sf.SFSeg((wl.nf, wl.h, wl.w), radii=(wl.rt, wl.ry, wl.rx),
-                   sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
-                   storage=args.storage)
-    K = wl.iters
-
-    def step(iters=K):
-        x.copy_(f)                                       # x0 = f
-        eng.power_iterate(f, f, x, iters, out=x)
+    kind = {"batch_24": Batch, "grad_48x480x854": Grad}.get(wl.name, SingleVideo)
+    prob = kind(wl, args.storage, rank, dev, sf, inputs)
+    K = prob.K
 
     def barrier():
         torch.cuda.synchronize()
@@ -193,55 +313,57 @@ def run_ours(args, wl):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        step()
+        prob.step(K)
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    launches0 = eng.launch_count()
+    launches0 = prob.eng.launch_count()
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            step()
+            prob.step(K)
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    launches = eng.launch_count() - launches0
-    tr = eng.trace()
-    xn = float(torch.linalg.vector_norm(x.double()))
+    launches = prob.eng.launch_count() - launches0
+    check = prob.check()
 
     # dominant kernel (the fused power step): the same calls with K and 0
     # steps, CUDA events on the launching stream; the difference is K step
-    # launches (plus a pointer-table write of a few bytes).
+    # launches (plus a pointer-table write of a few bytes).  For the
+    # differentiable form: the recorded forward with K and with 1 step.
     reps = max(3, args.steps // 2)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    e[0].record(stream)
-    for _ in range(reps):
-        step(K)
-    e[1].record(stream)
-    for _ in range(reps):
-        step(0)
-    e[2].record(stream)
-    torch.cuda.synchronize()
-    t_full = e[0].elapsed_time(e[1]) / reps
-    t_zero = e[1].elapsed_time(e[2]) / reps
-    step_ms = (t_full - t_zero) / K
+    if kind is Grad:
+        def fwd(k):
+            prob.x.copy_(prob.f)
+            prob.eng.power_iterate(prob.f, prob.f, prob.x, k, out=prob.x)
+        e[0].record(stream)
+        for _ in range(reps):
+            fwd(K)
+        e[1].record(stream)
+        for _ in range(reps):
+            fwd(1)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / (K - 1)
+    else:
+        e[0].record(stream)
+        for _ in range(reps):
+            prob.step(K)
+        e[1].record(stream)
+        for _ in range(reps):
+            prob.step(0)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / K
 
     # end to end through the public call with host buffers
-    f_host = torch.from_numpy(f_np).pin_memory()
-    out_host = torch.empty_like(f_host).pin_memory()
-    f_dev = torch.empty_like(f)
-
-    def e2e_step():
-        f_dev.copy_(f_host, non_blocking=True)
-        x.copy_(f_dev)
-        eng.power_iterate(f_dev, f_dev, x, K, out=x)
-        out_host.copy_(x, non_blocking=True)
-
     for _ in range(2):
-        e2e_step()
+        prob.e2e_step()
     barrier()
     e[0].record(stream)
     for _ in range(args.steps):
-        e2e_step()
+        prob.e2e_step()
     e[1].record(stream)
     barrier()
     e2e_ms = e[0].elapsed_time(e[1]) / args.steps
@@ -251,36 +373,70 @@ def run_ours(args, wl):
     if world > 1:
         torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
     ms, e2e_ms, step_ms = (float(v) for v in vals.cpu())
-    vox_iter = wl.n * K
+    vox_iter = prob.n * K
     value = world * vox_iter / (ms / 1e3)
     if rank == 0:
         peak, peak_kind = _peaks()
         bpv = 4 * STORAGE_BYTES[args.storage]          # read x, sp, f; write y
-        achieved = bpv * wl.n / (step_ms / 1e3) / 1e9
+        achieved = bpv * prob.n / (step_ms / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.storage, "data": "synthetic",
-            "config": workload_config(wl, args.storage),
+            "config": workload_config(wl, args.storage, prob),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "peak_kind": peak_kind, "kernel": "power step (fused stencil)",
                          "step_us": step_ms * 1e3, "bytes_per_voxel": bpv},
             "e2e": {"value": world * vox_iter / (e2e_ms / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(f_host.numel() * 4),
-                    "d2h_bytes_per_step": int(out_host.numel() * 4), "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": prob.h2d, "d2h_bytes_per_step": prob.d2h,
+                    "ms_per_step": e2e_ms},
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
-            "check": {"x_norm": xn, "rayleigh_last": float(tr["rayleigh"][-1]),
-                      "residual_last": float(tr["residual"][-1])},
+            "check": check,
         }
-        if args.cpu_baseline and world == 1:
+        if args.cpu_baseline and world == 1 and kind is SingleVideo:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line))
-    eng.close()
+    prob.eng.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_accuracy(args):
+    """Relative L2 and max-abs error of x^K (854x480x72, 50 steps) for FP32,
+    BF16 and FP16 storage against the FP64 oracle: on the same rounded
+    operands (kernel error) and on the FP32 operands (total error)."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1907_02731_gb300 as sf
+    from paper_1907_02731_gb300 import inputs
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    wl = inputs.WORKLOADS["video_72x480x854"]
+    f, _ = inputs.workload_video(wl.name)
+    radii, sig = (wl.rt, wl.ry, wl.rx), (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
+    sp32 = (f.astype(np.float32) ** np.float32(wl.p)).astype(np.float32)
+    refs, out = {}, {}
+    t0 = time.perf_counter()
+    for st in ("f32", "bf16", "f16"):
+        spr = oracle.to_storage(sp32, st).astype(np.float32)
+        fr = oracle.to_storage(f, st).astype(np.float32)
+        eng = sf.SFSeg(f.shape, radii=radii, sigmas=sig, alpha=wl.alpha, p=wl.p, storage=st,
+                       flags=sf.SFSEG_S_IS_SP)
+        d_sp, d_f = torch.from_numpy(spr).cuda(), torch.from_numpy(fr).cuda()
+        x = eng.power_iterate(d_sp, d_f, d_f.clone(), wl.iters).cpu().numpy().astype(np.float64)
+        eng.close()
+        refs[st] = oracle.power_iterate(spr, fr, fr, wl.iters, radii, sig, wl.alpha)["x"]
+        def err(a, b):
+            return {"rel_l2": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                    "max_abs": float(np.abs(a - b).max()), "max_ref": float(np.abs(b).max())}
+        out[st] = {"vs_oracle_same_operands": err(x, refs[st]),
+                   "vs_oracle_f32_operands": err(x, refs["f32"])}
+    print(json.dumps({"accuracy": out, "workload": wl.name, "iters": wl.iters,
+                      "oracle_seconds": time.perf_counter() - t0,
+                      "oracle_threads": int(os.environ["OMP_NUM_THREADS"])}))
 
 
 def main():
@@ -292,8 +448,13 @@ def main():
     ap.add_argument("--workload", default="video_72x480x854")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="report x^K errors of FP32/BF16/FP16 storage against the FP64 oracle")
     args = ap.parse_args()
     from paper_1907_02731_gb300 import inputs
+    if args.accuracy:
+        run_accuracy(args)
+        return
     wl = inputs.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

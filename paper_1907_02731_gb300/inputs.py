@@ -76,6 +76,8 @@ WORKLOADS = {
                                       5, 5, 1.5, 3.0, 50, 0.1, 1.0, 2, 3),
     "grad_48x480x854": Workload("grad_48x480x854", 48, 480, 854, 2, 5, 5, 1.5,
                                 3.0, 40, 1.0, 1.0, 2, 5),
+    # the uneven batch (shapes from batch_layout); nf/h/w here are unused
+    "batch_24": Workload("batch_24", 0, 0, 0, 2, 4, 4, 1.5, 2.5, 50, 0.1, 1.0, 2, 4),
 }
 
 # Uneven batch: 24 videos, frames U{20..120}, resolution from this set,
