@@ -65,6 +65,9 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     for (long i = 0; i < kWaitTries; ++i)
         if (mbar_try_wait(bar, parity)) return true;
@@ -160,7 +163,8 @@ struct Cfg {
     static constexpr int STAGE = 3 * ARR;
     static constexpr int YBC = TY * YBW * 4;                  // one channel of one Yb buffer
     static constexpr int YB = 3 * YBC;                        // one Yb buffer (3 channels)
-    static constexpr int SMEM = NS * STAGE + 2 * YB + NS * 8 + 128;
+    static constexpr int NBAR = NS + 4;                       // stages, FULL[2], EMPTY[2]
+    static constexpr int SMEM = NS * STAGE + 2 * YB + NBAR * 8 + 128;
     static_assert(NTA <= NA_WARPS * 32, "y-pass tasks exceed the y-pass warps");
     static_assert(RX <= XPAD && SC0 >= 0, "x radius exceeds the halo pad");
     static_assert(NS * STAGE >= NT * kRed * 8, "finalize scratch must fit in the stages");
@@ -174,14 +178,7 @@ __device__ __forceinline__ int quad_owner(int q) {
     return q < 2 ? 28 + q : (q < 30 ? q - 2 : q);
 }
 
-// Named barriers (id 0 is __syncthreads): Yb buffer b full / empty.
-__device__ __forceinline__ void nb_sync(int id) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(NT) : "memory");
-}
-__device__ __forceinline__ void nb_arrive(int id) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(NT) : "memory");
-}
-constexpr int BAR_FULL = 1, BAR_EMPTY = 3;   // + buffer index 0/1
+constexpr int NB_WARPS = NT / 32 - NA_WARPS;   // x-pass / temporal / combine warps
 
 // Temporal taps of one channel for ring phase U: frame tin feeds outputs
 // tin - RT + k with weight g_t(RT - k) (constant-bank operand); slot
@@ -219,40 +216,32 @@ __device__ __forceinline__ void tpass_phase(int u, float (&ring)[2 * RT + 1][4],
 }
 
 // x-pass of the three channels of one Yb row (channel planes TY * YBW apart):
-// lane owns quad own_q; the halo comes from the lanes owning the neighbour
-// quads (one shuffle per value); taps as constant-bank FMA operands.
+// lane l's outputs are Yb columns XPAD + 4l .. +3; its 4 + 2 RX input window
+// is read straight from shared memory with aligned 16-byte loads; taps as
+// constant-bank FMA operands.
 template <int RX>
-__device__ __forceinline__ void xpass3(const float* row, int own_q, int src_m2, int src_m1,
-                                       int src_p1, int src_p2, const float* gx, float (&p0)[4],
+__device__ __forceinline__ void xpass3(const float* row, int lane, const float* gx, float (&p0)[4],
                                        float (&p1)[4], float (&p2)[4]) {
-    float o[3][4];
+    constexpr int W0 = (XPAD - RX) & ~3;                    // aligned window start (column)
+    constexpr int NQ = (XPAD + 4 + RX - W0 + 3) / 4;        // float4 loads per channel
+    static_assert(4 * 27 + W0 + 4 * NQ <= YBW, "x window of the last output lane exceeds the row");
+    constexpr int SH = XPAD - RX - W0;                      // offset of column -RX in the window
+    float w[3][4 * NQ];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-        const float4 q = *reinterpret_cast<const float4*>(row + ch * TY * YBW + 4 * own_q);
-        o[ch][0] = q.x; o[ch][1] = q.y; o[ch][2] = q.z; o[ch][3] = q.w;
-    }
-    float w[3][4 + 2 * RX];
+    for (int ch = 0; ch < 3; ++ch)
 #pragma unroll
-    for (int c = -RX; c < 4 + RX; ++c) {
-        if (c >= 0 && c < 4) {
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) w[ch][c + RX] = o[ch][c];
-        } else {
-            const int qo = (c < 0) ? -((3 - c) / 4) : c / 4;   // floor(c / 4)
-            const int e = c - 4 * qo;
-            const int src = qo == -2 ? src_m2 : qo == -1 ? src_m1 : qo == 1 ? src_p1 : src_p2;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) w[ch][c + RX] = __shfl_sync(0xffffffffu, o[ch][e], src);
+        for (int q = 0; q < NQ; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(row + ch * TY * YBW + 4 * lane + W0 + 4 * q);
+            w[ch][4 * q] = v.x; w[ch][4 * q + 1] = v.y; w[ch][4 * q + 2] = v.z; w[ch][4 * q + 3] = v.w;
         }
-    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
         for (int d = 0; d <= 2 * RX; ++d) {
-            a0 = fmaf(w[0][i + d], gx[d], a0);
-            a1 = fmaf(w[1][i + d], gx[d], a1);
-            a2 = fmaf(w[2][i + d], gx[d], a2);
+            a0 = fmaf(w[0][SH + i + d], gx[d], a0);
+            a1 = fmaf(w[1][SH + i + d], gx[d], a1);
+            a2 = fmaf(w[2][SH + i + d], gx[d], a2);
         }
         p0[i] = a0;
         p1[i] = a1;
@@ -293,11 +282,13 @@ __device__ __forceinline__ void xpass(const float* row, int own_q, int src_m2, i
 
 // Warp roles.  Warps 0..3 ("A"): the elected thread issues the TMA loads one
 // frame ahead; all of them run the y-pass of frame p into Yb[vc % 2] (vc
-// counts the valid frames of the segment) and arrive on FULL.  Warps 4..15
-// ("B", one output row each): wait FULL, x-pass and temporal ring of the
-// three channels, combine of frame p - RT (its x, sp, f from the frame's
-// stage), store, then arrive on EMPTY.  A waits EMPTY of a buffer before
-// refilling it, so A runs at most two frames ahead of B's completed work.
+// counts the valid frames of the segment), then each A warp arrives once on
+// the FULL mbarrier of that buffer.  Warps 4..15 ("B", one output row each):
+// each waits on FULL on its own (the B warps are not coupled to each other),
+// x-pass and temporal ring of the three channels, combine of frame p - RT
+// (its x, sp, f from the frame's stage), store, then arrives once on EMPTY.
+// A waits until all B warps have arrived on EMPTY of a buffer before refilling
+// it, so A runs at most two frames ahead of B's completed work.
 // Stage reuse: with NS = RT + 3 stages and loads one frame ahead, the load of
 // frame p + 1 overwrites frame p - RT - 2, whose last reader (B's combine of
 // that frame, at B's frame p - 2) arrived on EMPTY before A passes its wait
@@ -318,12 +309,21 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     const int brow = warp - NA_WARPS;            // B: output row of the tile
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P.maps);
 
+    unsigned long long* full = bars + NS;       // [2], NA_WARPS arrivals per phase
+    unsigned long long* empty = bars + NS + 2;  // [2], NB_WARPS arrivals per phase
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&full[b]), NA_WARPS);
+            mbar_init(smem_u32(&empty[b]), NB_WARPS);
+        }
         fence_mbar_init();
         s_abort = 0;
     }
     __syncthreads();
+    // bit b: parity of the first FULL / EMPTY completion of buffer b in the
+    // current segment; use n of buffer b completes phase base ^ (n & 1)
+    unsigned fullbase = 0, emptybase = 0;
     // bit s: parity of the first completion of stage s in the current segment.
     // Inside a segment the valid frames p_first, p_first + 1, ... use stage
     // p % NS in turn, so frame p completes phase segphase[s] ^ ((p - p_first) / NS).
@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             for (int vc = 0; vc < n_valid; ++vc) {
                 const int p = p_first + vc;
                 const int b = vc & 1;
-                if (vc >= 2) nb_sync(BAR_EMPTY + b);
+                const unsigned n = (unsigned)(vc >> 1);
+                if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u)) s_abort = 1;
                 if (tid == 0 && vc + 1 < n_valid) issue(p + 1);
                 const int s = p % NS;
                 if (!mbar_wait(smem_u32(&bars[s]), parity(p))) {
@@ -429,7 +430,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                         *reinterpret_cast<float2*>(yc + 2 * TY * YBW + r) = q2[o];
                     }
                 }
-                nb_arrive(BAR_FULL + b);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full[b]));
             }
         } else {
             // ================= B: x-pass, temporal ring, combine ==============
@@ -460,9 +462,12 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                 float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
                 float p2[4] = {0.f, 0.f, 0.f, 0.f};
                 if (valid) {
-                    nb_sync(BAR_FULL + b);
+                    if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ (unsigned)(vc >> 1)) & 1u))
+                        s_abort = 1;
                     const float* row = yb + (b * 3 * TY + brow) * YBW;
-                    xpass3<RX>(row, own_q, src_m2, src_m1, src_p1, src_p2, P.gx, p0, p1, p2);
+                    // lanes 28..31 have no outputs: give them lane 27's window so
+                    // every read stays inside the row (columns <= XPAD + 4*27 + 4 + RX)
+                    xpass3<RX>(row, out_lane ? lane : 27, P.gx, p0, p1, p2);
                 }
                 float c0[4], c1[4], c2[4];
                 tpass_phase<RT>(u, r0, p0, P.gt, c0);
@@ -517,7 +522,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     }
                 }
                 if (valid) {
-                    if (vc + 2 < n_valid) nb_arrive(BAR_EMPTY + b);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&empty[b]));
                     ++vc;
                 }
             }
@@ -531,6 +537,12 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     if (owed & (1u << s)) (void)mbar_wait(smem_u32(&bars[s]), (owed_par >> s) & 1u);
             __syncthreads();
             return;
+        }
+        // buffer b was used (n_valid + 1 - b) / 2 times: FULL and EMPTY advanced
+        for (int b = 0; b < 2; ++b) {
+            const unsigned uses = (unsigned)((n_valid + 1 - b) / 2);
+            fullbase ^= (uses & 1u) << b;
+            emptybase ^= (uses & 1u) << b;
         }
         // every valid frame of the segment completed one phase of its stage
         for (int s = 0; s < NS; ++s) {
