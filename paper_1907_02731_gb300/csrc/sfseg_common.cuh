@@ -79,6 +79,9 @@ struct StepParams {
     float gy[2 * kMaxR + 1];
     float gx[2 * kMaxR + 1];
     // specialised kernel only
+    float2 gt2[2 * kMaxRt + 1];  // each tap twice, the paired operand of the packed FMAs
+    float2 gy2[2 * kMaxR + 1];
+    float2 gx2[2 * kMaxR + 1];
     const void* maps;           // [n_videos][4] CUtensorMap: sp, f, x_a, x_b (global memory)
     int x_sel;                  // 0: the input iterate is x_a, 1: x_b
     const int* cta_begin;       // [n_ctas + 1]: segments of CTA c are [cta_begin[c], cta_begin[c+1])
@@ -174,16 +177,18 @@ __device__ inline void finish_step(VState* st, double* trace_row, const double (
     if (st->tol > 0.0 && rho < st->tol * fabs(r)) st->done = 1;
 }
 
-// After a CTA of video v stored its FP64 partials (thread 0), the last CTA
-// of that video to arrive reduces all of them (fixed order) and runs
-// finish_step.  No CTA ever waits on another: the last one does the work.
-__device__ inline void arrive_and_finalize(const StepParams& P, int v, double* sh) {
+// After a CTA of video v stored the FP64 partials of n_arrive of the video's
+// items (thread 0), the last CTA of that video to arrive reduces all of them
+// (fixed order) and runs finish_step.  No CTA ever waits on another: the last
+// one does the work.
+__device__ inline void arrive_and_finalize(const StepParams& P, int v, double* sh,
+                                           unsigned n_arrive = 1u) {
     __shared__ int s_last;
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned cnt = (unsigned)(P.item_begin[v + 1] - P.item_begin[v]);
-        const unsigned prev = atomicAdd(&P.counters[v], 1u);
-        s_last = (prev + 1u == cnt);
+        const unsigned prev = atomicAdd(&P.counters[v], n_arrive);
+        s_last = (prev + n_arrive == cnt);
     }
     __syncthreads();
     if (!s_last) return;
@@ -199,11 +204,15 @@ __device__ inline void arrive_and_finalize(const StepParams& P, int v, double* s
     double* red = sh;   // blockDim * kRed doubles
     for (int c = 0; c < kRed; ++c) red[c * blockDim.x + threadIdx.x] = acc[c];
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
+    // halving folds; an odd count keeps its middle element for the next fold,
+    // so any block size works (for a power of two this is the plain tree)
+    for (int n = blockDim.x; n > 1;) {
+        const int h = (n + 1) / 2;
+        if ((int)threadIdx.x < n - h)
             for (int c = 0; c < kRed; ++c)
-                red[c * blockDim.x + threadIdx.x] += red[c * blockDim.x + threadIdx.x + s];
+                red[c * blockDim.x + threadIdx.x] += red[c * blockDim.x + threadIdx.x + h];
         __syncthreads();
+        n = h;
     }
     if (threadIdx.x == 0) {
         double S[kRed];

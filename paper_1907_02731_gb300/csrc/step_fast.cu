@@ -41,8 +41,10 @@
 namespace sfseg {
 namespace fast {
 
-constexpr int TX = 112, TY = 12, NT = 512, XPAD = 8, BOXW = TX + 2 * XPAD, YBW = BOXW;
+constexpr int TX = 112, TY = 12, XPAD = 8, BOXW = TX + 2 * XPAD, YBW = BOXW;
 constexpr int NA_WARPS = 4;                   // warps running the loads and the y-pass
+constexpr int NT = 32 * (NA_WARPS + TY);      // plus one x-pass/combine warp per tile row
+constexpr int LA = 1;                         // frames of TMA lookahead
 constexpr long kWaitTries = 1L << 24;         // bounded mbarrier wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -151,13 +153,14 @@ template <int RT, int RY, int RX, typename TS>
 struct Cfg {
     static constexpr int RXE = (RX + 1) & ~1;                 // x halo rounded to a column pair
     static constexpr int NPAIR = (TX + 2 * RXE) / 2;          // y-pass column pairs
-    static constexpr int NTA = 2 * NPAIR;                     // y-pass tasks: pair x 6 rows
-    static constexpr int TROWS = TY / 2;                      // output rows per y-pass task
+    static constexpr int NGRP = NA_WARPS * 32 / NPAIR;        // row groups of the y-pass
+    static constexpr int NTA = NGRP * NPAIR;                  // y-pass tasks: pair x TROWS rows
+    static constexpr int TROWS = TY / NGRP;                   // output rows per y-pass task
     static constexpr int SC0 = XPAD - RXE;                    // first y-pass stage column
     static constexpr int ROWS = TY + 2 * RY;                  // input rows per tile
     static constexpr int IN_ROWS = TROWS + 2 * RY;            // input rows per task
     static constexpr int NR = 2 * RT + 1;                     // temporal taps
-    static constexpr int NS = RT + 3;                         // stages (see the stage-reuse note)
+    static constexpr int NS = RT + 2 + LA;                    // stages (see the stage-reuse note)
     static constexpr int BOX_BYTES = ROWS * BOXW * (int)sizeof(TS);
     static constexpr int ARR = (BOX_BYTES + 127) / 128 * 128; // one array of a stage
     static constexpr int STAGE = 3 * ARR;
@@ -165,36 +168,36 @@ struct Cfg {
     static constexpr int YB = 3 * YBC;                        // one Yb buffer (3 channels)
     static constexpr int NBAR = NS + 4;                       // stages, FULL[2], EMPTY[2]
     static constexpr int SMEM = NS * STAGE + 2 * YB + NBAR * 8 + 128;
-    static_assert(NTA <= NA_WARPS * 32, "y-pass tasks exceed the y-pass warps");
+    static_assert(NTA <= NA_WARPS * 32 && TY % NGRP == 0, "y-pass tasks must tile the rows");
     static_assert(RX <= XPAD && SC0 >= 0, "x radius exceeds the halo pad");
     static_assert(NS * STAGE >= NT * kRed * 8, "finalize scratch must fit in the stages");
-    static_assert(NR <= 5, "the ring-phase switch covers 2 RT + 1 <= 5");
-    static_assert(SMEM <= 232448, "shared memory per block");
+        static_assert(SMEM <= 232448, "shared memory per block");
 };
-
-// Lane that owns quad q of a Yb row: quads 2..29 are the output lanes 0..27,
-// quads 0, 1 (left halo) and 30, 31 (right halo) belong to lanes 28..31.
-__device__ __forceinline__ int quad_owner(int q) {
-    return q < 2 ? 28 + q : (q < 30 ? q - 2 : q);
-}
 
 constexpr int NB_WARPS = NT / 32 - NA_WARPS;   // x-pass / temporal / combine warps
 
-// Temporal taps of one channel for ring phase U: frame tin feeds outputs
-// tin - RT + k with weight g_t(RT - k) (constant-bank operand); slot
-// (U - RT + k) mod NR holds output tin - RT + k.  Returns the finished
+// Packed (f32x2) and scalar multiply-add under one name, so that the temporal
+// ring code serves the paired (a, b) channels and the single c channel.
+__device__ __forceinline__ float2 pmul(float2 a, float2 g) { return __fmul2_rn(a, g); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 g, float2 c) { return __ffma2_rn(a, g, c); }
+__device__ __forceinline__ float pmul(float a, float g) { return a * g; }
+__device__ __forceinline__ float pfma(float a, float g, float c) { return fmaf(a, g, c); }
+
+// Temporal taps of one channel (or channel pair) for ring phase U: frame tin
+// feeds outputs tin - RT + k with weight g_t(RT - k) (constant-bank operand);
+// slot (U - RT + k) mod NR holds output tin - RT + k.  Returns the finished
 // output (slot of k = 0) in c.
-template <int U, int RT>
-__device__ __forceinline__ void tpass(float (&ring)[2 * RT + 1][4], const float (&p)[4],
-                                      const float* gt, float (&c)[4]) {
+template <int U, int RT, typename V>
+__device__ __forceinline__ void tpass(V (&ring)[2 * RT + 1][4], const V (&p)[4], const V* gt,
+                                      V (&c)[4]) {
     constexpr int NR = 2 * RT + 1;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const int slot = ((U - RT + k) % NR + NR) % NR;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (k == NR - 1) ring[slot][i] = p[i] * gt[k];
-            else ring[slot][i] = fmaf(p[i], gt[k], ring[slot][i]);
+            if (k == NR - 1) ring[slot][i] = pmul(p[i], gt[k]);
+            else ring[slot][i] = pfma(p[i], gt[k], ring[slot][i]);
         }
     }
     constexpr int slot0 = ((U - RT) % NR + NR) % NR;
@@ -202,97 +205,75 @@ __device__ __forceinline__ void tpass(float (&ring)[2 * RT + 1][4], const float 
     for (int i = 0; i < 4; ++i) c[i] = ring[slot0][i];
 }
 
-template <int RT>
-__device__ __forceinline__ void tpass_phase(int u, float (&ring)[2 * RT + 1][4], const float (&p)[4],
-                                            const float* gt, float (&c)[4]) {
-    constexpr int NR = 2 * RT + 1;
-    switch (u) {
-        case 0: tpass<0, RT>(ring, p, gt, c); break;
-        case 1: tpass<1 % NR, RT>(ring, p, gt, c); break;
-        case 2: tpass<2 % NR, RT>(ring, p, gt, c); break;
-        case 3: tpass<3 % NR, RT>(ring, p, gt, c); break;
-        default: tpass<4 % NR, RT>(ring, p, gt, c); break;
-    }
-}
+// The (a, b) plane of a Yb row is 64 chunks of 16 bytes (two columns each);
+// chunk k is stored at k ^ ((k >> 3) & 1), so that the x-pass windows (lane
+// stride two chunks) fall in eight distinct bank groups per 8-lane phase.
+__device__ __forceinline__ int ab_chunk(int k) { return k ^ ((k >> 3) & 1); }
 
-// x-pass of the three channels of one Yb row (channel planes TY * YBW apart):
-// lane l's outputs are Yb columns XPAD + 4l .. +3; its 4 + 2 RX input window
-// is read straight from shared memory with aligned 16-byte loads; taps as
-// constant-bank FMA operands.
+// x-pass of one Yb row.  Channels a and b are interleaved in Yb ((a, b) per
+// column, 8 bytes), so one packed FMA filters both; channel c has its own
+// plane.  Lane l's outputs are Yb columns XPAD + 4l .. +3; the input windows
+// are read straight from shared memory with aligned 16-byte loads; the taps
+// are constant-bank operands (paired for the packed FMAs).
 template <int RX>
-__device__ __forceinline__ void xpass3(const float* row, int lane, const float* gx, float (&p0)[4],
-                                       float (&p1)[4], float (&p2)[4]) {
-    constexpr int W0 = (XPAD - RX) & ~3;                    // aligned window start (column)
-    constexpr int NQ = (XPAD + 4 + RX - W0 + 3) / 4;        // float4 loads per channel
-    static_assert(4 * 27 + W0 + 4 * NQ <= YBW, "x window of the last output lane exceeds the row");
-    constexpr int SH = XPAD - RX - W0;                      // offset of column -RX in the window
-    float w[3][4 * NQ];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
+__device__ __forceinline__ void xpass_abc(const float* row_ab, const float* row_c, int lane,
+                                          const float2* gx2, const float* gx, float2 (&pab)[4],
+                                          float (&pc)[4]) {
+    {
+        constexpr int W0 = (XPAD - RX) & ~1;                 // first window column (even)
+        constexpr int SH = XPAD - RX - W0;                   // offset of column -RX in the window
+        constexpr int NQ = (SH + 4 + 2 * RX + 1) / 2;        // 16-byte loads (2 columns each)
+        static_assert(4 * 27 + W0 + 2 * NQ <= YBW && YBW % 16 == 0,
+                      "(a, b) window of the last output lane exceeds the row");
+        float2 w[2 * NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            const float4 v = *reinterpret_cast<const float4*>(row + ch * TY * YBW + 4 * lane + W0 + 4 * q);
-            w[ch][4 * q] = v.x; w[ch][4 * q + 1] = v.y; w[ch][4 * q + 2] = v.z; w[ch][4 * q + 3] = v.w;
+            const float4 v = *reinterpret_cast<const float4*>(row_ab + 4 * ab_chunk(2 * lane + W0 / 2 + q));
+            w[2 * q] = make_float2(v.x, v.y);
+            w[2 * q + 1] = make_float2(v.z, v.w);
         }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int i = 0; i < 4; ++i) {
+            float2 a = __fmul2_rn(w[SH + i], gx2[0]);
 #pragma unroll
-        for (int d = 0; d <= 2 * RX; ++d) {
-            a0 = fmaf(w[0][SH + i + d], gx[d], a0);
-            a1 = fmaf(w[1][SH + i + d], gx[d], a1);
-            a2 = fmaf(w[2][SH + i + d], gx[d], a2);
+            for (int d = 1; d <= 2 * RX; ++d) a = __ffma2_rn(w[SH + i + d], gx2[d], a);
+            pab[i] = a;
         }
-        p0[i] = a0;
-        p1[i] = a1;
-        p2[i] = a2;
     }
-}
-
-// x-pass of one channel of one Yb row: lane owns quad own_q; the halo comes
-// from the lanes owning the neighbour quads (one shuffle per value).
-template <int RX>
-__device__ __forceinline__ void xpass(const float* row, int own_q, int src_m2, int src_m1, int src_p1,
-                                      int src_p2, const float* gx, float (&out)[4]) {
-    float o[4];
     {
-        const float4 q = *reinterpret_cast<const float4*>(row + 4 * own_q);
-        o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
-    }
-    float w[4 + 2 * RX];
+        constexpr int W0 = (XPAD - RX) & ~3;                 // first window column (multiple of 4)
+        constexpr int SH = XPAD - RX - W0;
+        constexpr int NQ = (SH + 4 + 2 * RX + 3) / 4;        // 16-byte loads (4 columns each)
+        static_assert(4 * 27 + W0 + 4 * NQ <= YBW, "c window of the last output lane exceeds the row");
+        float w[4 * NQ];
 #pragma unroll
-    for (int c = -RX; c < 4 + RX; ++c) {
-        if (c >= 0 && c < 4) {
-            w[c + RX] = o[c];
-        } else {
-            const int qo = (c < 0) ? -((3 - c) / 4) : c / 4;   // floor(c / 4)
-            const int e = c - 4 * qo;
-            const int src = qo == -2 ? src_m2 : qo == -1 ? src_m1 : qo == 1 ? src_p1 : src_p2;
-            w[c + RX] = __shfl_sync(0xffffffffu, o[e], src);
+        for (int q = 0; q < NQ; ++q) {
+            const float4 v = *reinterpret_cast<const float4*>(row_c + 4 * lane + W0 + 4 * q);
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
         }
-    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float acc = 0.f;
+        for (int i = 0; i < 4; ++i) {
+            float a = w[SH + i] * gx[0];
 #pragma unroll
-        for (int d = 0; d <= 2 * RX; ++d) acc = fmaf(w[i + d], gx[d], acc);
-        out[i] = acc;
+            for (int d = 1; d <= 2 * RX; ++d) a = fmaf(w[SH + i + d], gx[d], a);
+            pc[i] = a;
+        }
     }
 }
 
-// Warp roles.  Warps 0..3 ("A"): the elected thread issues the TMA loads one
-// frame ahead; all of them run the y-pass of frame p into Yb[vc % 2] (vc
+// Warp roles.  Warps 0..3 ("A"): the elected thread issues the TMA loads LA
+// frames ahead; all of them run the y-pass of frame p into Yb[vc % 2] (vc
 // counts the valid frames of the segment), then each A warp arrives once on
-// the FULL mbarrier of that buffer.  Warps 4..15 ("B", one output row each):
+// the FULL mbarrier of that buffer.  Warps 4.. ("B", one output row each):
 // each waits on FULL on its own (the B warps are not coupled to each other),
 // x-pass and temporal ring of the three channels, combine of frame p - RT
 // (its x, sp, f from the frame's stage), store, then arrives once on EMPTY.
 // A waits until all B warps have arrived on EMPTY of a buffer before refilling
 // it, so A runs at most two frames ahead of B's completed work.
-// Stage reuse: with NS = RT + 3 stages and loads one frame ahead, the load of
-// frame p + 1 overwrites frame p - RT - 2, whose last reader (B's combine of
-// that frame, at B's frame p - 2) arrived on EMPTY before A passes its wait
-// at frame p.
+// Stage reuse: with NS = RT + 2 + LA stages and loads LA frames ahead, the
+// load of frame p + LA (issued at frame p, after A's EMPTY wait) overwrites
+// frame p - RT - 2, whose last reader (B's combine of that frame, at B's
+// frame p - 2) arrived on EMPTY before A passed that wait.
 template <int RT, int RY, int RX, typename TS>
 __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant__ StepParams P) {
     using C = Cfg<RT, RY, RX, TS>;
@@ -330,19 +311,29 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     unsigned segphase = 0;
     unsigned owed = 0, owed_par = 0;   // (thread 0) loads issued and not yet waited for
 
+    // Consecutive segments of one video form a run: the video's scalars are
+    // read once per run (they cannot change before every segment of the video
+    // has arrived), the FP64 sums accumulate over the run, and the run arrives
+    // once, counting all its segments.
     const int seg_b = P.cta_begin[blockIdx.x], seg_e = P.cta_begin[blockIdx.x + 1];
+    double acc[kRed] = {0.0, 0.0, 0.0, 0.0};
+    int run_v = -1, run_first = seg_b;
     for (int sg = seg_b; sg < seg_e; ++sg) {
         const WorkItem it = P.items[sg];
         const int v = it.video;
-        __syncthreads();   // every thread has read the previous segment's scalars
-        if (tid == 0) {
-            const VState* st = P.state + v;
-            s_skip = st->done;
-            s_scale = (float)st->scale;
-            s_gain = (float)st->gain;
-            s_shift = (float)(st->shift * st->scale);
+        if (v != run_v) {
+            __syncthreads();   // every thread has read the previous run's scalars
+            if (tid == 0) {
+                const VState* st = P.state + v;
+                s_skip = st->done;
+                s_scale = (float)st->scale;
+                s_gain = (float)st->gain;
+                s_shift = (float)(st->shift * st->scale);
+            }
+            __syncthreads();
+            run_v = v;
+            run_first = sg;
         }
-        __syncthreads();
         if (s_skip) continue;
         const VideoGeom g = P.geo[v];
         const int ta = it.t0, tb = it.t1, x0 = it.x0, y0 = it.y0;
@@ -352,7 +343,6 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
         auto parity = [&](int p) -> unsigned {
             return ((segphase >> (p % NS)) ^ (unsigned)((p - p_first) / NS)) & 1u;
         };
-        double acc[kRed] = {0.0, 0.0, 0.0, 0.0};
 
         if (is_a) {
             // ============================ A: loads + y-pass ====================
@@ -373,16 +363,15 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const int a_h = tid / C::NPAIR, a_p = tid - a_h * C::NPAIR;
             const int a_sc = C::SC0 + 2 * a_p;
             const bool a_task = tid < C::NTA;
-            float2 gy2[2 * RY + 1];
-#pragma unroll
-            for (int d = 0; d <= 2 * RY; ++d) gy2[d] = make_float2(P.gy[d], P.gy[d]);
-            if (tid == 0 && n_valid > 0) issue(p_first);
+            const float2* gy2 = P.gy2;
+            if (tid == 0)
+                for (int q = 0; q < LA && q < n_valid; ++q) issue(p_first + q);
             for (int vc = 0; vc < n_valid; ++vc) {
                 const int p = p_first + vc;
                 const int b = vc & 1;
                 const unsigned n = (unsigned)(vc >> 1);
                 if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u)) s_abort = 1;
-                if (tid == 0 && vc + 1 < n_valid) issue(p + 1);
+                if (tid == 0 && vc + LA < n_valid) issue(p + LA);
                 const int s = p % NS;
                 if (!mbar_wait(smem_u32(&bars[s]), parity(p))) {
                     s_abort = 1;
@@ -398,12 +387,6 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     const TS* sf = reinterpret_cast<const TS*>(st + 2 * C::ARR) + r0 * BOXW + a_sc;
                     float2 q0[C::TROWS], q1[C::TROWS], q2[C::TROWS];
 #pragma unroll
-                    for (int o = 0; o < C::TROWS; ++o) {
-                        q0[o] = make_float2(0.f, 0.f);
-                        q1[o] = make_float2(0.f, 0.f);
-                        q2[o] = make_float2(0.f, 0.f);
-                    }
-#pragma unroll
                     for (int i = 0; i < C::IN_ROWS; ++i) {
                         const float2 xv = Ld2<TS>::get(sx + i * BOXW);
                         const float2 sv = Ld2<TS>::get(ssp + i * BOXW);
@@ -414,20 +397,25 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 #pragma unroll
                         for (int o = 0; o < C::TROWS; ++o) {
                             const int d = i - o;
-                            if (d >= 0 && d <= 2 * RY) {
+                            if (d == 0) {              // first tap of output row o
+                                q0[o] = __fmul2_rn(b0, gy2[0]);
+                                q1[o] = __fmul2_rn(b1, gy2[0]);
+                                q2[o] = __fmul2_rn(b2, gy2[0]);
+                            } else if (d > 0 && d <= 2 * RY) {
                                 q0[o] = __ffma2_rn(b0, gy2[d], q0[o]);
                                 q1[o] = __ffma2_rn(b1, gy2[d], q1[o]);
                                 q2[o] = __ffma2_rn(b2, gy2[d], q2[o]);
                             }
                         }
                     }
+                    // Yb buffer: (a, b) interleaved plane [TY][YBW][2] (chunks swizzled), then the c plane [TY][YBW]
                     float* yc = yb + b * 3 * TY * YBW;
 #pragma unroll
                     for (int o = 0; o < C::TROWS; ++o) {
-                        const int r = (r0 + o) * YBW + a_sc;
-                        *reinterpret_cast<float2*>(yc + r) = q0[o];
-                        *reinterpret_cast<float2*>(yc + TY * YBW + r) = q1[o];
-                        *reinterpret_cast<float2*>(yc + 2 * TY * YBW + r) = q2[o];
+                        const int r = (r0 + o) * YBW;
+                        *reinterpret_cast<float4*>(yc + 2 * r + 4 * ab_chunk(a_sc / 2)) =
+                            make_float4(q0[o].x, q1[o].x, q0[o].y, q1[o].y);
+                        *reinterpret_cast<float2*>(yc + 2 * TY * YBW + r + a_sc) = q2[o];
                     }
                 }
                 __syncwarp();
@@ -437,9 +425,6 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             // ================= B: x-pass, temporal ring, combine ==============
             const float sg_s = s_scale * s_gain;     // deferred scale and gain
             const float alpha = P.alpha, shift = s_shift;
-            const int own_q = lane < 28 ? lane + 2 : (lane < 30 ? lane - 28 : lane);
-            const int src_m2 = quad_owner(max(own_q - 2, 0)), src_m1 = quad_owner(max(own_q - 1, 0));
-            const int src_p1 = quad_owner(min(own_q + 1, 31)), src_p2 = quad_owner(min(own_q + 2, 31));
             const bool out_lane = lane < 28;
             TS* Z = P.z_out ? (TS*)P.z_out + g.off : nullptr;
             float* FO = P.final_out ? P.final_out[v] : nullptr;
@@ -447,39 +432,53 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const int xg = x0 + 4 * lane;
             const bool st_ok = out_lane && yy < g.h;
 
-            float r0[NR][4], r1[NR][4], r2[NR][4];   // temporal rings, one per channel
+            float2 rab[NR][4];   // temporal ring of the (a, b) pair
+            float rc[NR][4];     // temporal ring of c
 #pragma unroll
             for (int k = 0; k < NR; ++k)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) r0[k][i] = r1[k][i] = r2[k][i] = 0.f;
+                for (int i = 0; i < 4; ++i) {
+                    rab[k][i] = make_float2(0.f, 0.f);
+                    rc[k][i] = 0.f;
+                }
             float part[kRed] = {0.f, 0.f, 0.f, 0.f};
-            int u = 0;             // ring phase of frame tin: (tin - (ta - RT)) mod NR
             int flush = 0;
             int vc = 0;
-            for (int tin = ta - RT; tin < t_end; ++tin) {
+            int tin = ta - RT;
+            // One input frame tin; U = (tin - (ta - RT)) mod NR is the ring phase,
+            // a compile-time constant, so the ring slots are fixed registers.
+            auto frame = [&](auto phase) {
+                constexpr int U = decltype(phase)::value;
                 const bool valid = (tin >= 0 && tin < g.nf);
                 const int b = vc & 1;
-                float p0[4] = {0.f, 0.f, 0.f, 0.f}, p1[4] = {0.f, 0.f, 0.f, 0.f};
-                float p2[4] = {0.f, 0.f, 0.f, 0.f};
+                float2 pab[4];
+                float pc[4];
                 if (valid) {
                     if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ (unsigned)(vc >> 1)) & 1u))
                         s_abort = 1;
-                    const float* row = yb + (b * 3 * TY + brow) * YBW;
+                    const float* yc = yb + b * 3 * TY * YBW;
                     // lanes 28..31 have no outputs: give them lane 27's window so
-                    // every read stays inside the row (columns <= XPAD + 4*27 + 4 + RX)
-                    xpass3<RX>(row, out_lane ? lane : 27, P.gx, p0, p1, p2);
+                    // every read stays inside the row
+                    xpass_abc<RX>(yc + 2 * brow * YBW, yc + (2 * TY + brow) * YBW, out_lane ? lane : 27,
+                                  P.gx2, P.gx, pab, pc);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        pab[i] = make_float2(0.f, 0.f);
+                        pc[i] = 0.f;
+                    }
                 }
-                float c0[4], c1[4], c2[4];
-                tpass_phase<RT>(u, r0, p0, P.gt, c0);
-                tpass_phase<RT>(u, r1, p1, P.gt, c1);
-                tpass_phase<RT>(u, r2, p2, P.gt, c2);
-                u = (u == NR - 1) ? 0 : u + 1;
+                float2 cab[4];
+                float c2[4];
+                tpass<U, RT>(rab, pab, P.gt2, cab);
+                tpass<U, RT>(rc, pc, P.gt, c2);
                 const int o = tin - RT;
                 if (o >= ta && o < tb) {
+                    // The load of frame o completed before A's y-pass of o (A waited
+                    // on the stage's mbarrier), and A's FULL arrival for o happened
+                    // after that wait; this warp has since observed FULL of o and of
+                    // the RT frames after it, so the load's bytes are visible here.
                     const int so = o % NS;
-                    // the frame's load completed long ago (A waited for it); this
-                    // wait returns at once and orders the reads after the load
-                    (void)mbar_wait(smem_u32(&bars[so]), parity(o));
                     const unsigned char* st = stages + so * C::STAGE;
                     const int off = (brow + RY) * BOXW + XPAD + 4 * lane;
                     float xs[4], sps[4], fs[4], z[4];
@@ -489,9 +488,9 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         // scale and gain applied here; t1 = f C0 - 2 C1
-                        const float t1 = fmaf(fs[i], c0[i], -2.f * c1[i]);
+                        const float t1 = fmaf(fs[i], cab[i].x, -2.f * cab[i].y);
                         const float t2 = fmaf(fs[i], t1, c2[i]);
-                        z[i] = (sg_s * sps[i]) * fmaf(-alpha, t2, c0[i]);
+                        z[i] = (sg_s * sps[i]) * fmaf(-alpha, t2, cab[i].x);
                     }
                     if (st_ok) {
                         if (FO) {
@@ -516,7 +515,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                             part[3] = fmaf(dz, dz, part[3]);
                         }
                     }
-                    if (++flush == 8) {
+                    if (++flush == 16) {          // at most 64 FP32 terms per lane
                         flush = 0;
                         warp_flush(part, acc);
                     }
@@ -526,6 +525,24 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     if (lane == 0) mbar_arrive(smem_u32(&empty[b]));
                     ++vc;
                 }
+                ++tin;
+            };
+            using I0 = std::integral_constant<int, 0>;
+            using I1 = std::integral_constant<int, 1 % NR>;
+            using I2 = std::integral_constant<int, 2 % NR>;
+            using I3 = std::integral_constant<int, 3 % NR>;
+            using I4 = std::integral_constant<int, 4 % NR>;
+            static_assert(NR == 5 || NR == 3, "the phase unroll covers 2 RT + 1 = 3 or 5");
+            while (tin < t_end) {
+                frame(I0{});
+                if (tin >= t_end) break;
+                frame(I1{});
+                if (tin >= t_end) break;
+                frame(I2{});
+                if (NR == 3 || tin >= t_end) continue;
+                frame(I3{});
+                if (tin >= t_end) break;
+                frame(I4{});
             }
             warp_flush(part, acc);
         }
@@ -550,16 +567,22 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const int cnt = (j < n_valid) ? (n_valid - 1 - j) / NS + 1 : 0;
             segphase ^= (unsigned)(cnt & 1) << s;
         }
-        {
+        if (sg + 1 == seg_e || P.items[sg + 1].video != v) {
+            // end of the run: its sum goes to the slot of its last segment, the
+            // other segments' slots get zeros, and the run arrives once
             const double sc = (double)s_scale;
             acc[1] *= sc;
             acc[2] *= sc * sc;
+            double* sh = reinterpret_cast<double*>(stages);
+            block_sum_lane0(acc, sh);
+            if (tid == 0) {
+                for (int q = run_first; q < sg; ++q)
+                    for (int c = 0; c < kRed; ++c) P.partials[(long long)q * kRed + c] = 0.0;
+                for (int c = 0; c < kRed; ++c) P.partials[(long long)sg * kRed + c] = acc[c];
+            }
+            arrive_and_finalize(P, v, sh, (unsigned)(sg - run_first + 1));
+            for (int c = 0; c < kRed; ++c) acc[c] = 0.0;
         }
-        double* sh = reinterpret_cast<double*>(stages);
-        block_sum_lane0(acc, sh);
-        if (tid == 0)
-            for (int c = 0; c < kRed; ++c) P.partials[(long long)sg * kRed + c] = acc[c];
-        arrive_and_finalize(P, v, sh);
         fence_proxy_async();   // generic writes to the stages precede the next TMA writes
         __syncthreads();
     }
