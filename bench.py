@@ -25,6 +25,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -141,14 +143,15 @@ def cpu_baseline(wl, seconds_hint: float = 15.0):
     import numpy as np
     import oracle
     from paper_1907_02731_gb300 import inputs
-    f, _ = inputs.workload_video(wl.name)
+    s, f = inputs.workload_features(wl.name)
     nf_s, iters = wl.nf, 4
-    sub = np.ascontiguousarray(f[:nf_s], dtype=np.float64)
+    sub = np.ascontiguousarray(s[:nf_s], dtype=np.float64)
+    fsub = np.ascontiguousarray(f[..., :nf_s, :, :], dtype=np.float64)
     radii = (wl.rt, wl.ry, wl.rx)
     sig = (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
     sp = oracle.unary(sub, wl.p)
     t0 = time.perf_counter()
-    oracle.power_iterate(sp, sub, sub, iters, radii, sig, wl.alpha)
+    oracle.power_iterate(sp, fsub, sub, iters, radii, sig, wl.alpha)
     dt = time.perf_counter() - t0
     vox_iter = sub.size * iters
     return {"value": vox_iter / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
@@ -183,7 +186,7 @@ def workload_config(wl, storage, prob=None):
     cfg = {"workload": wl.name, "frames": wl.nf, "h": wl.h, "w": wl.w,
            "kernel": f"{2 * wl.rx + 1}x{2 * wl.ry + 1}x{2 * wl.rt + 1}",
            "sigma_xy": wl.sigma_xy, "sigma_t": wl.sigma_t, "alpha": wl.alpha, "p": wl.p,
-           "iters_per_step": wl.iters, "storage": storage, "x0": "f",
+           "iters_per_step": wl.iters, "storage": storage, "x0": "f", "channels": wl.nchan,
            "l2": "operands larger than L2 (3 volumes of %.0f MB)" % (wl.n * 4 / 1e6)}
     if prob is not None and hasattr(prob, "dims"):
         cfg.update({"frames": None, "h": None, "w": None, "videos": len(prob.dims),
@@ -195,31 +198,35 @@ def workload_config(wl, storage, prob=None):
 
 
 class SingleVideo:
-    """One seeded video of a named workload (FP32 / BF16 / FP16 storage)."""
+    """One seeded video of a named workload (FP32 / BF16 / FP16 storage); with
+    several pairwise channels (Eq. 9) S is channel 0 and x0 = S."""
 
     def __init__(self, wl, storage, rank, dev, sf, inputs):
         import torch
         self.wl, self.K, self.n = wl, wl.iters, wl.n
-        seed = inputs.config_seed(wl.config, rank_video_index(rank))
-        self.f_np, _ = inputs.make_video(wl.nf, wl.h, wl.w, seed, wl.n_distractors)
-        self.f = torch.from_numpy(self.f_np).to(dev)
-        self.x = torch.empty_like(self.f)
+        s_np, f_np = inputs.workload_features(wl.name, rank_video_index(rank))
+        self.f_np = s_np
+        self.s = torch.from_numpy(s_np).to(dev)
+        self.f = self.s if wl.nchan == 1 else torch.from_numpy(f_np).to(dev)
+        self.x = torch.empty_like(self.s)
         self.eng = sf.SFSeg((wl.nf, wl.h, wl.w), radii=(wl.rt, wl.ry, wl.rx),
                             sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
-                            storage=storage)
-        self.f_host = torch.from_numpy(self.f_np).pin_memory()
-        self.out_host = torch.empty_like(self.f_host).pin_memory()
+                            storage=storage, nchan=wl.nchan)
+        self.f_host = torch.from_numpy(np.ascontiguousarray(f_np)).pin_memory()
+        self.out_host = torch.empty_like(self.s, device="cpu").pin_memory()
         self.f_dev = torch.empty_like(self.f)
-        self.h2d = self.d2h = int(self.f_host.numel() * 4)
+        self.h2d = int(self.f_host.numel() * 4)
+        self.d2h = int(self.out_host.numel() * 4)
 
     def step(self, iters):
-        self.x.copy_(self.f)                                       # x0 = f
-        self.eng.power_iterate(self.f, self.f, self.x, iters, out=self.x)
+        self.x.copy_(self.s)                                       # x0 = S
+        self.eng.power_iterate(self.s, self.f, self.x, iters, out=self.x)
 
     def e2e_step(self):
         self.f_dev.copy_(self.f_host, non_blocking=True)
-        self.x.copy_(self.f_dev)
-        self.eng.power_iterate(self.f_dev, self.f_dev, self.x, self.K, out=self.x)
+        s_dev = self.f_dev if self.wl.nchan == 1 else self.f_dev[0]   # S = channel 0
+        self.x.copy_(s_dev)
+        self.eng.power_iterate(s_dev, self.f_dev, self.x, self.K, out=self.x)
         self.out_host.copy_(self.x, non_blocking=True)
 
     def check(self):
@@ -402,7 +409,7 @@ def run_ours(args, wl):
     value = job_units / (ms / 1e3)
     if rank == 0:
         peak, peak_kind = _peaks()
-        bpv = 4 * STORAGE_BYTES[args.storage]          # read x, sp, f; write y
+        bpv = (3 + wl.nchan) * STORAGE_BYTES[args.storage]   # read x, sp, f_1..f_C; write y
         achieved = bpv * prob.n / (step_ms / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -412,7 +419,9 @@ def run_ours(args, wl):
             "config": workload_config(wl, args.storage, prob),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "peak_kind": peak_kind, "kernel": "power step (fused stencil)",
+                         "peak_kind": peak_kind,
+                         "kernel": "power step (fused stencil%s)" % (
+                             ", any-radius kernel, %d channels" % wl.nchan if wl.nchan > 1 else ""),
                          "step_us": step_ms * 1e3, "bytes_per_voxel": bpv},
             "e2e": {"value": job_units / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": prob.h2d, "d2h_bytes_per_step": prob.d2h,

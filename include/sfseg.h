@@ -74,7 +74,12 @@ typedef struct {
     double p;                /* unary exponent: sp = S^p, >= 0 */
     int32_t storage;         /* sfseg_dtype */
     int32_t flags;           /* SFSEG_* flags above */
-    int32_t nchan;           /* pairwise feature channels C >= 1 (Eq. 9); d_f is [C][nf][h][w] */
+    int32_t nchan;           /* pairwise feature channels C (Eq. 9), 1 <= C <= 4; d_f is [C][nf][h][w].
+                              * M_ij = sp_i sp_j sum_c [1 - alpha (f_ci - f_cj)^2] G_ij, evaluated
+                              * with C + 2 convolutions.  C > 1 runs on the any-radius step kernel;
+                              * SFSEG_EUNSUPPORTED when its buffers for the given radii exceed
+                              * shared memory, and for the adjoint and the no-alloc entry point
+                              * (both C = 1 only). */
     int32_t ckpt_every;      /* adjoint checkpoint interval in steps (0 = 8) */
 } sfseg_params;
 

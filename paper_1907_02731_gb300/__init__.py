@@ -251,11 +251,13 @@ def _dev_f32(t, name):
 class SFSeg:
     """One context for volumes of shape (nf, h, w) (or a batch of shapes).
 
-    ``radii`` = (rt, ry, rx), ``sigmas`` = (sigma_t, sigma_y, sigma_x).
+    ``radii`` = (rt, ry, rx), ``sigmas`` = (sigma_t, sigma_y, sigma_x);
+    ``nchan`` > 1 sums the affinities of several pairwise feature channels
+    (Eq. 9), ``f`` then being a contiguous [nchan, nf, h, w] tensor.
     """
 
     def __init__(self, shape=None, *, radii=(2, 5, 5), sigmas=(1.5, 3.0, 3.0), alpha=1.0,
-                 p=0.1, storage="f32", flags=0, batch_shapes=None, ckpt_every=8):
+                 p=0.1, storage="f32", flags=0, batch_shapes=None, ckpt_every=8, nchan=1):
         nf, h, w = shape if shape is not None else (1, 1, 1)
         prm = sfseg_default_params(nf, h, w)
         prm.rt, prm.ry, prm.rx = radii
@@ -264,6 +266,7 @@ class SFSeg:
         prm.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
         prm.flags = flags
         prm.ckpt_every = ckpt_every
+        prm.nchan = nchan              # Eq. 9 channels: f is then [nchan, nf, h, w]
         self.params = prm
         self.batch_shapes = [tuple(s) for s in batch_shapes] if batch_shapes else None
         self.shape = tuple(shape) if shape is not None else None

@@ -105,6 +105,10 @@ extern "C" sfseg_status sfseg_power_iterate_noalloc(const sfseg_params* prm, con
                                                     double* d_trace, void* stream) {
     sfseg_status st = validate_params(prm);
     if (st != SFSEG_OK) return st;
+    if (prm->nchan != 1) {
+        set_global_error("no-alloc path: one pairwise channel only");
+        return SFSEG_EUNSUPPORTED;
+    }
     if (!d_s || !d_f || !d_x) {
         set_global_error("no-alloc path: d_s, d_f and d_x must be non-NULL");
         return SFSEG_EINVAL;
@@ -163,6 +167,7 @@ extern "C" sfseg_status sfseg_power_iterate_noalloc(const sfseg_params* prm, con
     StepParams P{};
     P.sp = B + o_sp;
     P.f = B + o_f;
+    P.nchan = 1;
     P.geo = (const VideoGeom*)(B + o_geo);
     P.state = (VState*)(B + o_state);
     P.items = (const WorkItem*)(B + o_items);

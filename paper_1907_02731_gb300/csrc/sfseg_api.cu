@@ -114,8 +114,12 @@ static sfseg_status validate(const sfseg_params* p) {
         return fail(nullptr, SFSEG_EINVAL, "storage %d is not an sfseg_dtype", p->storage);
     if (p->nchan < 1 || p->nchan > 8)
         return fail(nullptr, SFSEG_EINVAL, "nchan %d outside [1, 8]", p->nchan);
-    if (p->nchan != 1)
-        return fail(nullptr, SFSEG_EUNSUPPORTED, "nchan > 1 (Eq. 9) is not built yet");
+    if (p->nchan > kMaxChan)
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "nchan %d: at most %d channels are built", p->nchan, kMaxChan);
+    if (generic_smem_bytes(p->rt, p->ry, p->rx, p->nchan) > generic_smem_cap())
+        return fail(nullptr, SFSEG_EUNSUPPORTED,
+                    "nchan %d with radii (%d,%d,%d): the step's buffers exceed shared memory", p->nchan,
+                    p->rt, p->ry, p->rx);
     if (p->ckpt_every < 0) return fail(nullptr, SFSEG_EINVAL, "ckpt_every must be >= 0");
     return SFSEG_OK;
 }
@@ -299,7 +303,8 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         off += (g.nf * g.plane + align - 1) / align * align;
         c->geo.push_back(g);
     }
-    c->fast = !(prm->flags & SFSEG_GENERIC) && fast_available(prm->rt, prm->ry, prm->rx, prm->storage);
+    c->fast = !(prm->flags & SFSEG_GENERIC) && prm->nchan == 1 &&
+              fast_available(prm->rt, prm->ry, prm->rx, prm->storage);
     std::vector<WorkItem> items;
     std::vector<int> cta_begin, vseg;
     if (c->fast) {
@@ -484,6 +489,8 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
     memcpy(P.gt, c->gt, sizeof c->gt);
     memcpy(P.gy, c->gy, sizeof c->gy);
     memcpy(P.gx, c->gx, sizeof c->gx);
+    P.nchan = c->prm.nchan;
+    P.fstride = c->total;
     for (int d = 0; d < 2 * kMaxRt + 1; ++d) P.gt2[d] = make_float2(P.gt[d], P.gt[d]);
     for (int d = 0; d < 2 * kMaxR + 1; ++d) {
         P.gy2[d] = make_float2(P.gy[d], P.gy[d]);

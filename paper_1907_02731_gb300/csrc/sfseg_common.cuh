@@ -21,6 +21,7 @@ constexpr int kMaxR = 16;       // largest spatial radius
 constexpr int kMaxRt = 8;       // largest temporal radius
 constexpr int kRed = 4;         // reductions per step: z.z, xh.z, xh.xh, |z - s xh|^2
 constexpr int kMaxDynSmem = 232448;   // dynamic shared memory per block (227 KB)
+constexpr int kMaxChan = 4;           // pairwise feature channels (Eq. 9) of the step kernels
 
 // Per-step record of the forward pass for the adjoint (per video, nullable):
 // scale[k] turns the stored iterate of step k into the unit-norm x^k (k = 0..K),
@@ -78,6 +79,8 @@ struct StepParams {
     float gt[2 * kMaxRt + 1];
     float gy[2 * kMaxR + 1];
     float gx[2 * kMaxR + 1];
+    int nchan;                  // pairwise feature channels C (Eq. 9); f holds C volumes
+    long long fstride;          // elements between consecutive channel volumes of f
     // specialised kernel only
     float2 gt2[2 * kMaxRt + 1];  // each tap twice, the paired operand of the packed FMAs
     float2 gy2[2 * kMaxR + 1];

@@ -105,7 +105,8 @@ sfseg_status validate_params(const sfseg_params* p);
 void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- steps
-size_t generic_smem_bytes(int rt, int ry, int rx);
+size_t generic_smem_bytes(int rt, int ry, int rx, int nchan = 1);
+size_t generic_smem_cap();
 void generic_tile(int* tx, int* ty);
 cudaError_t setup_step_generic(int rt, int ry, int rx);
 cudaError_t launch_step_generic(int storage, const StepParams& P, int n_items, cudaStream_t s);

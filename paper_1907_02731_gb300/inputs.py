@@ -58,6 +58,7 @@ class Workload:
     alpha: float
     n_distractors: int
     config: int
+    nchan: int = 1          # pairwise feature channels (Eq. 9)
 
     @property
     def n(self) -> int:
@@ -78,6 +79,11 @@ WORKLOADS = {
                                 3.0, 40, 1.0, 1.0, 2, 5),
     # the uneven batch (shapes from batch_layout); nf/h/w here are unused
     "batch_24": Workload("batch_24", 0, 0, 0, 2, 4, 4, 1.5, 2.5, 50, 0.1, 1.0, 2, 4),
+    # two pairwise channels (Eq. 9), as with the paper's forward and backward
+    # optical-flow magnitudes: S = channel 0 = the video, channel 1 a second
+    # seeded video of the same shape
+    "video2ch_72x480x854": Workload("video2ch_72x480x854", 72, 480, 854, 2, 5, 5, 1.5, 3.0, 50,
+                                    0.1, 1.0, 2, 6, nchan=2),
 }
 
 # Uneven batch: 24 videos, frames U{20..120}, resolution from this set,
@@ -151,6 +157,24 @@ def workload_video(name: str, index: int = 0):
     wl = WORKLOADS[name]
     return make_video(wl.nf, wl.h, wl.w, config_seed(wl.config, index),
                       wl.n_distractors)
+
+
+def channel_seed(config: int, index: int, channel: int) -> int:
+    """Seed of pairwise channel ``channel`` >= 1 of video ``index``."""
+    return config_seed(config, index) + 7919 * int(channel)
+
+
+def workload_features(name: str, index: int = 0):
+    """(s, f) of a named workload: s = the seeded video; f = s for one
+    channel, else [nchan, nf, h, w] with channel 0 = s and channel c a video
+    drawn from ``channel_seed``."""
+    wl = WORKLOADS[name]
+    s, _ = make_video(wl.nf, wl.h, wl.w, config_seed(wl.config, index), wl.n_distractors)
+    if wl.nchan == 1:
+        return s, s
+    chans = [s] + [make_video(wl.nf, wl.h, wl.w, channel_seed(wl.config, index, c),
+                              wl.n_distractors)[0] for c in range(1, wl.nchan)]
+    return s, np.ascontiguousarray(np.stack(chans))
 
 
 def batch_layout(n_videos: int = BATCH_VIDEOS, config: int = BATCH_CONFIG):

@@ -62,3 +62,25 @@ def test_null_context_calls(lib):
     assert lib.sfseg_get_trace(None, 0, None, None, None, 0) == -1
     lib.sfseg_destroy(None)
     assert lib.sfseg_launch_count(None) == 0
+
+
+@pytest.mark.parametrize("nchan,radii", [(5, (2, 5, 5)), (8, (1, 1, 1)), (4, (8, 16, 16)),
+                                         (3, (8, 16, 16))])
+def test_create_rejects_unsupported_channels(lib, nchan, radii):
+    """Eq. 9 channels: at most 4, and only while the any-radius kernel's
+    buffers for these radii fit in shared memory (host-side check)."""
+    p = sf.sfseg_default_params(4, 8, 8)
+    p.nchan = nchan
+    p.rt, p.ry, p.rx = radii
+    with pytest.raises(sf.SFSegError) as ei:
+        sf.sfseg_create(p)
+    assert ei.value.status == sf.SFSEG_EUNSUPPORTED
+    assert "nchan" in sf.sfseg_last_error(None)
+
+
+def test_noalloc_rejects_channels(lib):
+    p = sf.sfseg_default_params(4, 8, 8)
+    p.nchan = 2
+    with pytest.raises(sf.SFSegError) as ei:
+        sf.sfseg_power_iterate_noalloc(p, 1, 1, 1, 3)
+    assert ei.value.status == sf.SFSEG_EUNSUPPORTED

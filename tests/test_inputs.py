@@ -33,3 +33,25 @@ def test_batch_layout():
     assert dims == inputs.batch_layout()
     vids = inputs.batch_videos(n_videos=3, scale=0.1)
     assert len(vids) == 3 and all(v.ndim == 3 for v in vids)
+
+
+def test_workload_features_channels():
+    """Eq. 9 workload: channel 0 is the video S, the other channel a distinct
+    seeded video of the same shape; single-channel workloads return f = s."""
+    from paper_1907_02731_gb300 import inputs
+    wl = inputs.WORKLOADS["video2ch_72x480x854"]
+    assert wl.nchan == 2
+    small = dict(nf=3, h=20, w=30)
+    import dataclasses
+    inputs.WORKLOADS["_tiny2ch"] = dataclasses.replace(wl, name="_tiny2ch", **small)
+    try:
+        s, f = inputs.workload_features("_tiny2ch")
+        s2, f2 = inputs.workload_features("_tiny2ch")
+        assert f.shape == (2, 3, 20, 30) and f.dtype == np.float32
+        np.testing.assert_array_equal(f[0], s)
+        assert not np.array_equal(f[1], f[0])
+        np.testing.assert_array_equal(f, f2)
+    finally:
+        del inputs.WORKLOADS["_tiny2ch"]
+    s1, f1 = inputs.workload_features("small_16x64x64")
+    assert f1 is s1

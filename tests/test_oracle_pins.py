@@ -217,6 +217,28 @@ def test_conv_form_equals_explicit_multichannel():
     assert rel(y_edge, y_sum) < 1e-14
 
 
+def test_multichannel_special_cases():
+    """Eq. 9 reduces to known operators: C identical channels give C times the
+    single-channel M (same iterates, Rayleigh quotient times C); a channel that
+    is zero everywhere adds sp_i sp_j G_ij, i.e. D G D with D = diag(sp)."""
+    rng = np.random.default_rng(17)
+    shape, radii, sig, alpha = (4, 6, 7), (1, 2, 2), (1.0, 1.5, 1.5), 0.8
+    sp = oracle.unary(rng.random(shape), 0.1)
+    f = rng.random(shape)
+    x = rng.random(shape)
+    y1 = oracle.apply_M(sp, f, x, radii, sig, alpha)
+    for C in (2, 3):
+        yC = oracle.apply_M(sp, np.stack([f] * C), x, radii, sig, alpha)
+        assert rel(yC, C * y1) < 1e-14
+        r1 = oracle.power_iterate(sp, f, x, 6, radii, sig, alpha)
+        rC = oracle.power_iterate(sp, np.stack([f] * C), x, 6, radii, sig, alpha)
+        assert rel(rC["x"], r1["x"]) < 1e-13
+        np.testing.assert_allclose(rC["rayleigh"], C * np.asarray(r1["rayleigh"]), rtol=1e-12)
+    y0 = oracle.apply_M(sp, np.stack([f, np.zeros(shape)]), x, radii, sig, alpha)
+    ydgd = oracle.apply_M(sp, f, x, radii, sig, 0.0)          # alpha = 0: D G D x
+    assert rel(y0, y1 + ydgd) < 1e-14
+
+
 # -------------------------------------------- brute force + dense eigh (Fig. 3)
 @pytest.mark.parametrize("shape", [(6, 10, 10), (2, 3, 4)])
 def test_dense_matrix_and_eigh(shape):
