@@ -135,6 +135,37 @@ sfseg_status sfseg_power_iterate_batched(sfseg_ctx* ctx, const float* const* d_s
                                          const float* const* d_f, float* const* d_x,
                                          int32_t n_iters, void* stream);
 
+/* Binarisation schedule (Alg. 1 Step 3 and Sec. 4 "Binarization - Spectral
+ * vs Discrete space"): after a few power steps in the continuous space the
+ * iterate is projected through a sigmoid and the next step starts from the
+ * projection; after the last step a hard threshold gives the segmentation.
+ * The paper gives no values; with u = x / max(x) (x >= 0 by
+ * Perron-Frobenius):
+ *   after step j (1-based), k0 <= j < n_iters:  x <- p / ||p||,
+ *                                      p = 1 / (1 + exp(-beta (u - tau)));
+ *   after the last step:              mask = [u >= theta]  (FP32 compare).
+ * sfseg_default_binarize: k0 = 3, beta = 10, tau = 0.5, theta = 0.5. */
+typedef struct {
+    int32_t k0;              /* first step followed by a projection, >= 1 */
+    int32_t reserved;        /* 0 */
+    double beta;             /* sigmoid steepness, finite, >= 0 */
+    double tau;              /* sigmoid centre on u, finite */
+    double theta;            /* final threshold on u, finite */
+} sfseg_binarize;
+
+void sfseg_default_binarize(sfseg_binarize* b);
+
+/* sfseg_power_iterate with the binarisation schedule (single-video
+ * contexts; not with SFSEG_RECORD).  d_x: in x0, out the unit-L2 x^K (FP32);
+ * d_mask: nullable device [nf][h][w] bytes (0/1), the hard segmentation of
+ * x^K; the trace records r_k, rho_k, ||M x^k|| of every step (x^k being the
+ * projected iterate where a projection preceded step k).  Runs step by step
+ * (no CUDA graph).  Errors: as sfseg_power_iterate, and EINVAL for bad
+ * schedule parameters or a batched context. */
+sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* ctx, const float* d_s, const float* d_f,
+                                           float* d_x, int32_t n_iters, const sfseg_binarize* b,
+                                           uint8_t* d_mask, void* stream);
+
 /* Rayleigh quotient lambda = x.Mx / x.x (Eq. 3 read as a Rayleigh quotient)
  * and residual ||Mx - lambda x|| / ||x|| of d_x ([nf][h][w] FP32, device)
  * with the features loaded last.  Synchronises the stream.

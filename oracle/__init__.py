@@ -14,6 +14,8 @@ Contents
     3D-convolution form of Eq. 7 with direct (non-separable) convolutions; it
     exists to check Eq. 4 == Eq. 7 and is used by that test only.
   * ``dense.py``: brute-force dense M for tiny volumes (eigendecomposition).
+  * ``binarize.py``: Algorithm 1 with the binarisation step (sigmoid
+    projections, final hard threshold) on top of the edge-by-edge M.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, special cases, dense eigendecomposition, finite differences).

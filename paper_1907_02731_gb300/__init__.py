@@ -32,7 +32,15 @@ EXPORTS = (
     "sfseg_power_iterate_batched", "sfseg_rayleigh", "sfseg_apply", "sfseg_get_trace",
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
     "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
+    "sfseg_default_binarize", "sfseg_power_iterate_binarized",
 )
+
+
+class sfseg_binarize(ctypes.Structure):
+    """Binarisation schedule (Alg. 1 Step 3): projection after steps k0.. of
+    p = sigmoid(beta (x / max x - tau)), final mask x >= theta max x."""
+    _fields_ = [("k0", ctypes.c_int32), ("reserved", ctypes.c_int32), ("beta", ctypes.c_double),
+                ("tau", ctypes.c_double), ("theta", ctypes.c_double)]
 
 
 class sfseg_params(ctypes.Structure):
@@ -87,6 +95,9 @@ def load_library(path: str = LIB_PATH):
         "sfseg_power_iterate_noalloc": (_i32, [P, _vp, _vp, _vp, _i32, _vp, _vp]),
         "sfseg_plan_segments": (_i32, [_i32, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32),
                                        _i32, ctypes.POINTER(_i32), _i32]),
+        "sfseg_default_binarize": (None, [ctypes.POINTER(sfseg_binarize)]),
+        "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
+                                                 ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -218,6 +229,18 @@ def sfseg_power_iterate_noalloc(params: sfseg_params, d_s: int, d_f: int, d_x: i
                                                       n_iters, d_trace, stream))
 
 
+def sfseg_default_binarize() -> sfseg_binarize:
+    b = sfseg_binarize()
+    load_library().sfseg_default_binarize(ctypes.byref(b))
+    return b
+
+
+def sfseg_power_iterate_binarized(ctx, d_s, d_f, d_x, n_iters: int, b: sfseg_binarize,
+                                  d_mask=None, stream: int = 0) -> None:
+    _check(load_library().sfseg_power_iterate_binarized(ctx, d_s, d_f, d_x, n_iters, ctypes.byref(b),
+                                                        d_mask, stream), ctx)
+
+
 def sfseg_plan_segments(dims, n_sms: int):
     """Work decomposition of the specialised kernel (host only): returns
     (segments [n][5] as (video, x0, y0, t0, t1), cta_begin list)."""
@@ -299,6 +322,22 @@ class SFSeg:
         self.iters_done = sfseg_power_iterate(self.ctx, ds, df, _dev_f32(x, "x").data_ptr(), iters,
                                               tol, want_iters_done=tol > 0, stream=_stream_handle())
         return x
+
+    def power_iterate_binarized(self, s, f, x0, iters: int, k0: int = 3, beta: float = 10.0,
+                                tau: float = 0.5, theta: float = 0.5, out=None):
+        """x^K with the binarisation schedule of Alg. 1 (sigmoid projections
+        after steps k0..K-1) and the hard mask x^K >= theta max(x^K) (uint8)."""
+        import torch
+        x = out if out is not None else torch.empty_like(_dev_f32(x0, "x0"))
+        if x.data_ptr() != x0.data_ptr():
+            x.copy_(x0)
+        mask = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+        b = sfseg_binarize(k0=k0, reserved=0, beta=beta, tau=tau, theta=theta)
+        ds = _dev_f32(s, "s").data_ptr() if s is not None else None
+        df = _dev_f32(f, "f").data_ptr() if f is not None else None
+        sfseg_power_iterate_binarized(self.ctx, ds, df, _dev_f32(x, "x").data_ptr(), iters, b,
+                                      mask.data_ptr(), _stream_handle())
+        return x, mask
 
     def power_iterate_batched(self, s_list, f_list, x_list, iters: int):
         """In place on ``x_list`` (x0 in, x^K out)."""

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <map>
 #include <string>
@@ -58,6 +59,8 @@ struct sfseg_ctx {
     double* d_rrec = nullptr;   // the same for the backward's recompute
     int ckpt_cap = 0;
     void* d_ckpt = nullptr;     // [ckpt_cap] volumes: x^{j C} (and x^K last)
+    // binarisation scratch (allocated on first use): 2 max keys + block partials
+    unsigned char* d_bin = nullptr;
     void* d_adj = nullptr;      // [C + 4] volumes: recompute ring, g ping-pong, dsp, df
     int adj_cap = 0;
     double* d_adjc = nullptr;   // [2] dot products
@@ -136,7 +139,7 @@ static void free_ctx(sfseg_ctx* c) {
                     c->d_partials, c->d_counters, c->d_prep_partials, c->d_prep_counter, c->d_bad,
                     c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps,
                     c->d_gitems, c->d_gitem_begin, c->d_gpartials, c->d_rec, c->d_rrec,
-                    c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter};
+                    c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter, c->d_bin};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -797,6 +800,94 @@ sfseg_status sfseg_power_iterate(sfseg_ctx* c, const float* d_s, const float* d_
     }
     const float* xin = d_x;
     return iterate_impl(c, &xin, &d_x, n_iters, tol, iters_done, s);
+}
+
+void sfseg_default_binarize(sfseg_binarize* b) {
+    if (!b) return;
+    b->k0 = 3;
+    b->reserved = 0;
+    b->beta = 10.0;
+    b->tau = 0.5;
+    b->theta = 0.5;
+}
+
+static constexpr int kBinBlocks = 1216;   // 8 blocks of 256 threads per SM on 152 SMs
+
+sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* c, const float* d_s, const float* d_f,
+                                           float* d_x, int32_t n_iters, const sfseg_binarize* b,
+                                           uint8_t* d_mask, void* stream) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (c->batched) return fail(c, SFSEG_EINVAL, "binarisation takes a single-video context");
+    if (!b) return fail(c, SFSEG_EINVAL, "schedule is NULL");
+    if (b->k0 < 1 || !std::isfinite(b->beta) || b->beta < 0.0 || !std::isfinite(b->tau) ||
+        !std::isfinite(b->theta))
+        return fail(c, SFSEG_EINVAL, "schedule: k0 >= 1, beta finite >= 0, tau and theta finite");
+    if (n_iters < 1) return fail(c, SFSEG_EINVAL, "n_iters must be >= 1");
+    if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
+    if (c->prm.flags & SFSEG_RECORD)
+        return fail(c, SFSEG_EUNSUPPORTED, "binarisation does not record for the adjoint");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((d_s == nullptr) != (d_f == nullptr))
+        return fail(c, SFSEG_EINVAL, "pass both d_s and d_f, or neither");
+    if (d_s) {
+        sfseg_status st = load_features_impl(c, &d_s, &d_f, s);
+        if (st != SFSEG_OK) return st;
+    }
+    if (!c->features) return fail(c, SFSEG_ESTATE, "no features loaded");
+    sfseg_status st = ensure_trace(c, n_iters);
+    if (st != SFSEG_OK) return st;
+    if (!c->d_bin) {
+        const size_t bytes = 16 + sizeof(double) * kBinBlocks;
+        CUDA_OR(c, cudaMalloc((void**)&c->d_bin, bytes));
+        CUDA_OR(c, cudaMemset(c->d_bin, 0, bytes));
+    }
+    unsigned* keys = reinterpret_cast<unsigned*>(c->d_bin);
+    double* partials = reinterpret_cast<double*>(c->d_bin + 16);
+    c->recorded = false;
+    st = prep_x(c, 0, d_x, false, 0.0, s);
+    if (st != SFSEG_OK) return st;
+    const VideoGeom& g = c->geo[0];
+    const int nblk = (int)std::min<long long>(kBinBlocks, (g.n + 255) / 256);
+    const int K = n_iters;
+    for (int k = 0; k < K; ++k) {
+        if (k == K - 1) {
+            CUDA_OR(c, launch_set_ptrs(c->d_out, &d_x, 1, s));
+            c->launches += 1;
+            CUDA_OR(c, launch_step(c, k, true, true, s));
+        } else {
+            CUDA_OR(c, launch_step(c, k, false, true, s));
+        }
+        if (k + 1 < K && k + 1 >= b->k0) {   // Alg. 1 Step 3 after step k + 1 (1-based)
+            ProjectParams P{};
+            P.buf = ((k + 1) & 1) ? c->xb : c->xa;   // where step k stored its output
+            P.g = g;
+            P.state = c->d_state;
+            P.video = 0;
+            P.beta = (float)b->beta;
+            P.tau = (float)b->tau;
+            P.vmax_key = keys;
+            P.partials = partials;
+            P.n_blocks = nblk;
+            CUDA_OR(c, launch_project(c->prm.storage, P, s));
+            c->launches += 3;
+        }
+    }
+    FinishParams F{};
+    F.out = d_x;
+    F.buf0 = c->xa;
+    F.buf1 = c->xb;
+    F.g = g;
+    F.state = c->d_state;
+    F.video = 0;
+    F.final_iter = K;
+    CUDA_OR(c, launch_finish(c->prm.storage, F, s));
+    c->launches += 1;
+    if (d_mask) {
+        CUDA_OR(c, launch_threshold(d_x, g.n, keys + 1, (float)b->theta, d_mask, nblk, s));
+        c->launches += 2;
+    }
+    c->last_stream = s;
+    return SFSEG_OK;
 }
 
 sfseg_status sfseg_power_iterate_batched(sfseg_ctx* c, const float* const* d_s,

@@ -59,6 +59,22 @@ struct FinishParams {
 cudaError_t launch_prep_features(int storage, const PrepFeatParams& P, cudaStream_t s);
 cudaError_t launch_prep_x(int storage, const PrepXParams& P, int blocks, cudaStream_t s);
 cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s);
+
+// binarisation (Alg. 1 Step 3): projection of a video's stored iterate, and
+// the final threshold of the caller's FP32 result
+struct ProjectParams {
+    void* buf;                  // packed stored iterate (storage type), projected in place
+    VideoGeom g;
+    VState* state;
+    int video;
+    float beta, tau;            // p = 1 / (1 + exp(-beta (x / max x - tau)))
+    unsigned* vmax_key;         // order-preserving key of max x (0 before the call)
+    double* partials;           // [n_blocks]
+    int n_blocks;
+};
+cudaError_t launch_project(int storage, const ProjectParams& P, cudaStream_t s);
+cudaError_t launch_threshold(const float* x, long long n, unsigned* key, float theta, unsigned char* mask,
+                             int n_blocks, cudaStream_t s);
 cudaError_t launch_set_ptrs(float** dst, float* const* src, int n, cudaStream_t s);
 int prep_x_blocks(long long n);
 

@@ -239,6 +239,61 @@ def test_multichannel_special_cases():
     assert rel(y0, y1 + ydgd) < 1e-14
 
 
+def test_binarized_reduces_to_plain_iteration():
+    """k0 >= K: no projection, the plain power iteration."""
+    from oracle import binarize
+    rng = np.random.default_rng(23)
+    shape, radii, sig = (3, 8, 9), (1, 2, 2), (1.0, 1.5, 1.5)
+    sp = oracle.unary(rng.random(shape), 0.1)
+    f = rng.random(shape)
+    x0 = rng.random(shape)
+    b = binarize.power_iterate_binarized(sp, f, x0, 6, radii, sig, 1.0, 6, 10.0, 0.5, 0.5)
+    r = oracle.power_iterate(sp, f, x0, 6, radii, sig, 1.0)
+    assert rel(b["x"], r["x"]) < 1e-13
+    np.testing.assert_allclose(b["rayleigh"], r["rayleigh"], rtol=1e-13)
+
+
+def test_binarized_beta_zero_restarts_from_uniform():
+    """beta = 0 projects every voxel to 1/2 after every step from k0 on, so
+    the last step starts from the uniform vector: x^K = M 1 / ||M 1||."""
+    from oracle import binarize
+    rng = np.random.default_rng(29)
+    shape, radii, sig = (4, 7, 8), (1, 2, 2), (1.0, 1.5, 1.5)
+    sp = oracle.unary(rng.random(shape), 0.1)
+    f = rng.random(shape)
+    x0 = rng.random(shape)
+    K, k0 = 7, 3
+    b = binarize.power_iterate_binarized(sp, f, x0, K, radii, sig, 1.0, k0, 0.0, 0.3, 0.5)
+    r = oracle.power_iterate(sp, f, np.ones(shape), 1, radii, sig, 1.0)
+    assert rel(b["x"], r["x"]) < 1e-13
+    # and the Rayleigh quotients of steps k0 .. K-1 are those of the uniform vector
+    r1 = oracle.power_iterate(sp, f, np.ones(shape), 1, radii, sig, 1.0)["rayleigh"][0]
+    np.testing.assert_allclose(b["rayleigh"][k0:], r1, rtol=1e-13)
+
+
+def test_binarized_two_voxel_by_hand():
+    """The worked two-voxel example (M = [[4, 3/8], [3/8, 1/4]]) with one
+    projection after step 1, values by hand: y1 = M (1, 2) = (19/4, 7/8),
+    u = (1, 7/38); p = (s(beta (1 - tau)), s(beta (7/38 - tau))), s the
+    logistic function; then y2 = M p / ||p|| and the mask at theta."""
+    from oracle import binarize
+    shape = (1, 1, 2)
+    sp = np.array([2.0, 0.5]).reshape(shape)
+    f = np.array([0.0, 0.5]).reshape(shape)
+    x0 = np.array([1.0, 2.0]).reshape(shape)
+    beta, tau = 4.0, 0.5
+    out = binarize.power_iterate_binarized(sp, f, x0, 2, (0, 0, 1), (1, 1, SIGMA_DYADIC), 1.0, 1,
+                                           beta, tau, 0.2)
+    logistic = lambda t: 1.0 / (1.0 + math.exp(-t))
+    p = np.array([logistic(beta * (1 - tau)), logistic(beta * (7 / 38 - tau))])
+    p /= np.linalg.norm(p)
+    y2 = np.array([4 * p[0] + 0.375 * p[1], 0.375 * p[0] + 0.25 * p[1]])
+    np.testing.assert_allclose(out["x"].ravel(), y2 / np.linalg.norm(y2), rtol=1e-14)
+    assert abs(out["rayleigh"][1] - float(p @ y2)) < 1e-14
+    u2 = y2 / y2.max()
+    np.testing.assert_array_equal(out["mask"].ravel(), (u2 >= 0.2).astype(np.uint8))
+
+
 # -------------------------------------------- brute force + dense eigh (Fig. 3)
 @pytest.mark.parametrize("shape", [(6, 10, 10), (2, 3, 4)])
 def test_dense_matrix_and_eigh(shape):
