@@ -473,6 +473,49 @@ def run_accuracy(args):
                       "oracle_threads": int(os.environ["OMP_NUM_THREADS"])}))
 
 
+SWEEP_SHAPES = ((10, 20, 20), (10, 60, 107), (20, 120, 214), (36, 240, 427), (72, 480, 854))
+
+
+def run_sweep(args):
+    """Runtime of one power step against the number of nodes (Fig. 2): the
+    same 11x11x5 kernel and seeded video recipe from the paper's 4000-node toy
+    to the full 854x480x72 video; one JSON line per size."""
+    import torch
+    import paper_1907_02731_gb300 as sf
+    from paper_1907_02731_gb300 import inputs
+    wl = inputs.WORKLOADS["video_72x480x854"]
+    for shape in SWEEP_SHAPES:
+        f_np, _ = inputs.make_video(*shape, inputs.config_seed(wl.config, 0), wl.n_distractors)
+        f = torch.from_numpy(f_np).cuda()
+        x = torch.empty_like(f)
+        eng = sf.SFSeg(shape, radii=(wl.rt, wl.ry, wl.rx), sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy),
+                       alpha=wl.alpha, p=wl.p, storage=args.storage)
+
+        def call(k):
+            x.copy_(f)
+            eng.power_iterate(f, f, x, k, out=x)
+        for _ in range(max(args.warmup, 3)):
+            call(wl.iters)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        reps = max(args.steps, 5)
+        e[0].record()
+        for _ in range(reps):
+            call(wl.iters)
+        e[1].record()
+        for _ in range(reps):
+            call(0)
+        e[2].record()
+        torch.cuda.synchronize()
+        step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / wl.iters
+        n = int(np.prod(shape))
+        print(json.dumps({"sweep": "power step vs nodes", "shape": list(shape), "nodes": n,
+                          "storage": args.storage, "us_per_step": step_ms * 1e3,
+                          "voxel_iter_per_s": n / (step_ms / 1e3),
+                          "call_ms_50_steps": e[0].elapsed_time(e[1]) / reps}))
+        eng.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -484,7 +527,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--accuracy", action="store_true",
                     help="report x^K errors of FP32/BF16/FP16 storage against the FP64 oracle")
+    ap.add_argument("--sweep", action="store_true",
+                    help="time one power step at sizes from 4000 nodes to the full video")
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     from paper_1907_02731_gb300 import inputs
     if args.accuracy:
         run_accuracy(args)
