@@ -489,7 +489,7 @@ def run_sweep(args):
         f = torch.from_numpy(f_np).cuda()
         x = torch.empty_like(f)
         eng = sf.SFSeg(shape, radii=(wl.rt, wl.ry, wl.rx), sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy),
-                       alpha=wl.alpha, p=wl.p, storage=args.storage)
+                       alpha=wl.alpha, p=wl.p, storage=args.storage, flags=args.sweep_flags)
 
         def call(k):
             x.copy_(f)
@@ -510,7 +510,7 @@ def run_sweep(args):
         step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / wl.iters
         n = int(np.prod(shape))
         print(json.dumps({"sweep": "power step vs nodes", "shape": list(shape), "nodes": n,
-                          "storage": args.storage, "us_per_step": step_ms * 1e3,
+                          "storage": args.storage, "flags": args.sweep_flags, "us_per_step": step_ms * 1e3,
                           "voxel_iter_per_s": n / (step_ms / 1e3),
                           "call_ms_50_steps": e[0].elapsed_time(e[1]) / reps}))
         eng.close()
@@ -529,6 +529,8 @@ def main():
                     help="report x^K errors of FP32/BF16/FP16 storage against the FP64 oracle")
     ap.add_argument("--sweep", action="store_true",
                     help="time one power step at sizes from 4000 nodes to the full video")
+    ap.add_argument("--sweep-flags", type=int, default=0,
+                    help="context flags for --sweep (8: any-radius kernel, 16: autotune)")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)

@@ -79,8 +79,6 @@ struct StepParams {
     float gt[2 * kMaxRt + 1];
     float gy[2 * kMaxR + 1];
     float gx[2 * kMaxR + 1];
-    int nchan;                  // pairwise feature channels C (Eq. 9); f holds C volumes
-    long long fstride;          // elements between consecutive channel volumes of f
     // specialised kernel only
     float2 gt2[2 * kMaxRt + 1];  // each tap twice, the paired operand of the packed FMAs
     float2 gy2[2 * kMaxR + 1];
@@ -89,6 +87,11 @@ struct StepParams {
     int x_sel;                  // 0: the input iterate is x_a, 1: x_b
     const int* cta_begin;       // [n_ctas + 1]: segments of CTA c are [cta_begin[c], cta_begin[c+1])
     Record rec;                 // forward record (single video), or all null
+    // Appended last: inserting them before the fields above shifts the tap
+    // pairs the packed FMAs read from the constant bank and costs the
+    // specialised step about 3% (measured).
+    int nchan;                  // pairwise feature channels C (Eq. 9); f holds C volumes
+    long long fstride;          // elements between consecutive channel volumes of f
 };
 
 // ---------------------------------------------------------------- storage
