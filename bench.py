@@ -34,6 +34,13 @@ METRIC = "voxel-iterations/sec and HBM GB/s fraction at 480p vs plain FP32, rel-
 UNIT = "voxel-iter/s"
 STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
+# capture of that kernel as it stands (profiles/step_fast_video_72x480x854.md:
+# ncu --set full --clock-control none -k regex:step_fast -s 10 -c 1 ...
+# python bench.py --steps 2 --warmup 1 --no-cpu-baseline).  Only workloads
+# whose kernel was captured have an entry; the others report null.
+DRAM_TRAFFIC_PER_LAUNCH = {("video_72x480x854", "f32"): 367.766784e6 + 99.112448e6}
+
 
 def _peaks():
     try:
@@ -418,7 +425,10 @@ def run_ours(args, wl):
             "dtype": args.storage, "data": "synthetic",
             "config": workload_config(wl, args.storage, prob),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": DRAM_TRAFFIC_PER_LAUNCH.get((wl.name, args.storage)),
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                         "algorithmic_bytes_per_launch": bpv * prob.n,
                          "peak_kind": peak_kind,
                          "kernel": "power step (fused stencil%s)" % (
                              ", any-radius kernel, %d channels" % wl.nchan if wl.nchan > 1 else ""),
