@@ -1024,8 +1024,29 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
     int cur = 0, cpar = 0;
     for (int m = nseg - 1; m >= 0; --m) {
         const int k0 = m * C, k1 = (k0 + C < K) ? k0 + C : K;
-        // recompute x^{k0+1} .. x^{k1-1} from the checkpoint with the generic step
-        if (k1 - k0 > 1) {
+        // recompute x^{k0+1} .. x^{k1-1} from the checkpoint with the step kernel
+        // of the forward: the specialised one reproduces the recorded iterates
+        // bit for bit (same kernel, plan and operands); it runs through the
+        // context's ping-pong buffers (they carry the TMA descriptors) and each
+        // output is copied to its adjoint volume
+        if (k1 - k0 > 1 && c->fast) {
+            CUDA_OR(c, launch_set_state(c->d_state, rscale + k0, rgain + k0, k0, s));
+            c->launches += 1;
+            CUDA_OR(c, cudaMemcpyAsync(c->xa, ckpt_ptr(c, m), vb, cudaMemcpyDeviceToDevice, s));
+            for (int k = k0; k < k1 - 1; ++k) {
+                const int i = k - k0;
+                StepParams P = step_params(c, i, false, true);   // reads buffer i & 1
+                P.trace = nullptr;
+                P.trace_cap = 0;
+                P.rec.scale = qscale;
+                P.rec.gain = qscale + (c->rec_cap + 1);
+                P.rec.ny = qscale + 2 * (c->rec_cap + 1);
+                CUDA_OR(c, launch_step_fast(c->prm.storage, P, c->n_ctas, s));
+                c->launches += 1;
+                CUDA_OR(c, cudaMemcpyAsync(vol(i + 1), ((i + 1) & 1) ? c->xb : c->xa, vb,
+                                           cudaMemcpyDeviceToDevice, s));
+            }
+        } else if (k1 - k0 > 1) {
             CUDA_OR(c, launch_set_state(c->d_state, rscale + k0, rgain + k0, k0, s));
             c->launches += 1;
             for (int k = k0; k < k1 - 1; ++k) {
