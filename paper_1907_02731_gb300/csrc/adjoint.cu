@@ -191,6 +191,77 @@ __global__ void __launch_bounds__(256) pitch_copy_kernel(const float* src, float
 }
 
 // Per-video state for recomputing forward steps from a checkpoint.
+// ---- reverse step on the specialised forward kernel (FP32):
+// 1. uprep: u_k = (g_{k+1} - c x^{k+1}) / ||y_k||, c = x^{k+1}.g_{k+1}, into a
+//    buffer the forward kernel reads;
+// 2. the forward kernel on u with scale = gain = 1 gives g_k = M u_k and, as
+//    its adjoint terms, K_U and F_U (the recompute of step k gave K_X, F_X of
+//    the stored x^k, to be scaled by s_cur);
+// 3. adj_combine: dL/dsp += u K_X s_cur + x K_U, dL/df += -2 alpha sp
+//    (u F_X s_cur + x F_U), x = s_cur * stored x^k, and x^k.g_k for the next
+//    (earlier) step, g_k = sp K_U.
+__global__ void __launch_bounds__(256) uprep_kernel(const float* g_in, const float* x_next, const double* s_next,
+                                                    const double* c, const double* ny, float* u_out,
+                                                    VideoGeom g) {
+    const long long n = g.n, hw = (long long)g.h * g.w;
+    const float cs = (float)(*c * *s_next), inv = (float)(1.0 / *ny);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
+        const long long o = g.off + t * g.plane + yy * g.pitch + xx;
+        u_out[o] = (g_in[o] - cs * x_next[o]) * inv;
+    }
+}
+
+__global__ void __launch_bounds__(256) adj_combine_kernel(const __grid_constant__ AdjCombineParams P) {
+    const VideoGeom g = P.g;
+    const long long n = g.n, hw = (long long)g.h * g.w;
+    const float s_cur = (float)*P.s_cur, m2a = -2.f * P.alpha;
+    float part = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
+        const long long o = g.off + t * g.plane + yy * g.pitch + xx;
+        const float u = P.u[o], x = s_cur * P.x_cur[o], s = P.sp[o];
+        const float ku = P.ku[o], fu = P.fu[o];
+        const float kx = s_cur * P.kx[o], fx = s_cur * P.fx[o];
+        P.dsp[o] += fmaf(u, kx, x * ku);
+        P.df[o] += m2a * s * fmaf(u, fx, x * fu);
+        part = fmaf(x, s * ku, part);                 // x^k . g_k, g_k = sp K_U
+    }
+    const float w = warp_sum(part);
+    __shared__ double sh[32];
+    __shared__ int s_last;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += sh[k];
+        P.partials[blockIdx.x] = b;
+        __threadfence();
+        s_last = (atomicAdd(P.counter, 1u) + 1u == gridDim.x);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(&P.partials[b]);
+        *P.c_out = tot;
+        *P.counter = 0u;
+    }
+}
+
+cudaError_t launch_uprep(const float* g_in, const float* x_next, const double* s_next, const double* c,
+                         const double* ny, float* u_out, const VideoGeom& g, int blocks, cudaStream_t s) {
+    uprep_kernel<<<blocks, 256, 0, s>>>(g_in, x_next, s_next, c, ny, u_out, g);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_adj_combine(const AdjCombineParams& P, int blocks, cudaStream_t s) {
+    adj_combine_kernel<<<blocks, 256, 0, s>>>(P);
+    return cudaPeekAtLastError();
+}
+
 __global__ void set_state_kernel(VState* st, const double* scale, const double* gain, int iter) {
     VState s{};
     s.scale = *scale;

@@ -61,6 +61,8 @@ struct sfseg_ctx {
     void* d_ckpt = nullptr;     // [ckpt_cap] volumes: x^{j C} (and x^K last)
     // binarisation scratch (allocated on first use): 2 max keys + block partials
     unsigned char* d_bin = nullptr;
+    // reverse step on the specialised kernel: scratch state, constants, partials
+    unsigned char* d_adj_misc = nullptr;
     void* d_adj = nullptr;      // [C + 4] volumes: recompute ring, g ping-pong, dsp, df
     int adj_cap = 0;
     double* d_adjc = nullptr;   // [2] dot products
@@ -139,7 +141,8 @@ static void free_ctx(sfseg_ctx* c) {
                     c->d_partials, c->d_counters, c->d_prep_partials, c->d_prep_counter, c->d_bad,
                     c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps,
                     c->d_gitems, c->d_gitem_begin, c->d_gpartials, c->d_rec, c->d_rrec,
-                    c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter, c->d_bin};
+                    c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter, c->d_bin,
+                    c->d_adj_misc};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -994,13 +997,24 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
     const size_t vb = vol_bytes(c);
     if (setup_adjoint(c->prm.rt, c->prm.ry, c->prm.rx) != cudaSuccess)
         return fail(c, SFSEG_EUNSUPPORTED, "radii too large for the adjoint tile");
-    if (c->adj_cap < C + 4) {
+    // volumes: recomputed iterates [C], g ping-pong [2], dL/dsp, dL/df; on the
+    // specialised path also K_X, F_X of every recomputed step [2C], K_U, F_U
+    const int nvol = c->fast ? 3 * C + 6 : C + 4;
+    if (c->adj_cap < nvol) {
         CUDA_OR(c, cudaDeviceSynchronize());
         if (c->d_adj) cudaFree(c->d_adj);
         c->d_adj = nullptr;
         c->adj_cap = 0;
-        CUDA_OR(c, cudaMalloc(&c->d_adj, vb * (C + 4)));
-        c->adj_cap = C + 4;
+        CUDA_OR(c, cudaMalloc(&c->d_adj, vb * nvol));
+        c->adj_cap = nvol;
+    }
+    constexpr int kAdjBlocks = 1216;
+    if (c->fast && !c->d_adj_misc) {
+        const size_t bytes = 256 + sizeof(double) * kAdjBlocks;
+        CUDA_OR(c, cudaMalloc((void**)&c->d_adj_misc, bytes));
+        CUDA_OR(c, cudaMemset(c->d_adj_misc, 0, bytes));
+        const double ones[2] = {1.0, 1.0};
+        CUDA_OR(c, cudaMemcpy(c->d_adj_misc + 128, ones, sizeof ones, cudaMemcpyHostToDevice));
     }
     if (!c->d_adjc) {
         CUDA_OR(c, cudaMalloc((void**)&c->d_adjc, sizeof(double) * 2));
@@ -1016,7 +1030,7 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
     const double* rgain = c->d_rec + (c->rec_cap + 1);
     const double* rny = c->d_rec + 2 * (c->rec_cap + 1);
     double* qscale = c->d_rrec;   // scales of the recomputed iterates
-    CUDA_OR(c, cudaMemsetAsync(c->d_adj, 0, vb * (C + 4), s));
+    CUDA_OR(c, cudaMemsetAsync(c->d_adj, 0, vb * nvol, s));
     CUDA_OR(c, launch_pitch_copy(d_gx, gb[0], g, 1, nullptr, s));
     CUDA_OR(c, launch_dot((const float*)ckpt_ptr(c, nseg), rscale + K, gb[0], g, c->d_prep_partials,
                           c->d_prep_counter, c->d_adjc, prep_x_blocks(g.n), s));
@@ -1029,11 +1043,12 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
         // bit for bit (same kernel, plan and operands); it runs through the
         // context's ping-pong buffers (they carry the TMA descriptors) and each
         // output is copied to its adjoint volume
-        if (k1 - k0 > 1 && c->fast) {
+        if (c->fast) {
+            // every step of the segment, the last one for its adjoint terms only
             CUDA_OR(c, launch_set_state(c->d_state, rscale + k0, rgain + k0, k0, s));
             c->launches += 1;
             CUDA_OR(c, cudaMemcpyAsync(c->xa, ckpt_ptr(c, m), vb, cudaMemcpyDeviceToDevice, s));
-            for (int k = k0; k < k1 - 1; ++k) {
+            for (int k = k0; k < k1; ++k) {
                 const int i = k - k0;
                 StepParams P = step_params(c, i, false, true);   // reads buffer i & 1
                 P.trace = nullptr;
@@ -1041,11 +1056,61 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
                 P.rec.scale = qscale;
                 P.rec.gain = qscale + (c->rec_cap + 1);
                 P.rec.ny = qscale + 2 * (c->rec_cap + 1);
+                P.aux_k = vol(C + 4 + i);
+                P.aux_f = vol(2 * C + 4 + i);
                 CUDA_OR(c, launch_step_fast(c->prm.storage, P, c->n_ctas, s));
                 c->launches += 1;
-                CUDA_OR(c, cudaMemcpyAsync(vol(i + 1), ((i + 1) & 1) ? c->xb : c->xa, vb,
-                                           cudaMemcpyDeviceToDevice, s));
+                if (k + 1 < k1)
+                    CUDA_OR(c, cudaMemcpyAsync(vol(i + 1), ((i + 1) & 1) ? c->xb : c->xa, vb,
+                                               cudaMemcpyDeviceToDevice, s));
             }
+            VState* ustate = reinterpret_cast<VState*>(c->d_adj_misc);
+            const double* one = reinterpret_cast<const double*>(c->d_adj_misc + 128);
+            unsigned* cnt = reinterpret_cast<unsigned*>(c->d_adj_misc + 192);
+            double* part = reinterpret_cast<double*>(c->d_adj_misc + 256);
+            float* ku = vol(3 * C + 4);
+            float* fu = vol(3 * C + 5);
+            const int nblk = (int)std::min<long long>(kAdjBlocks, (g.n + 255) / 256);
+            for (int k = k1 - 1; k >= k0; --k) {
+                const float* x_next = (k + 1 == k1) ? (const float*)ckpt_ptr(c, m + 1) : vol(k + 1 - k0);
+                const double* s_next = (k + 1 == k1) ? rscale + k1 : qscale + k + 1;
+                const float* x_cur = (k == k0) ? (const float*)ckpt_ptr(c, m) : vol(k - k0);
+                const double* s_cur = (k == k0) ? rscale + k0 : qscale + k;
+                // u_k into the forward kernel's input buffer
+                CUDA_OR(c, launch_uprep(gb[cur], x_next, s_next, c->d_adjc + cpar, rny + k, (float*)c->xa, g,
+                                        nblk, s));
+                // g_k = M u_k, with K_U and F_U
+                CUDA_OR(c, launch_set_state(ustate, one, one + 1, 0, s));
+                StepParams P = step_params(c, 0, false, true);
+                P.z_out = gb[1 - cur];
+                P.state = ustate;
+                P.trace = nullptr;
+                P.trace_cap = 0;
+                P.aux_k = ku;
+                P.aux_f = fu;
+                CUDA_OR(c, launch_step_fast(c->prm.storage, P, c->n_ctas, s));
+                AdjCombineParams Q{};
+                Q.u = (const float*)c->xa;
+                Q.x_cur = x_cur;
+                Q.sp = (const float*)c->sp;
+                Q.ku = ku;
+                Q.fu = fu;
+                Q.kx = vol(C + 4 + (k - k0));
+                Q.fx = vol(2 * C + 4 + (k - k0));
+                Q.dsp = dsp;
+                Q.df = df;
+                Q.s_cur = s_cur;
+                Q.c_out = c->d_adjc + (1 - cpar);
+                Q.partials = part;
+                Q.counter = cnt;
+                Q.g = g;
+                Q.alpha = (float)c->prm.alpha;
+                CUDA_OR(c, launch_adj_combine(Q, nblk, s));
+                c->launches += 4;
+                cur = 1 - cur;
+                cpar = 1 - cpar;
+            }
+            continue;
         } else if (k1 - k0 > 1) {
             CUDA_OR(c, launch_set_state(c->d_state, rscale + k0, rgain + k0, k0, s));
             c->launches += 1;

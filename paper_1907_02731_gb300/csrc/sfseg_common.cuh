@@ -92,6 +92,11 @@ struct StepParams {
     // specialised step about 3% (measured).
     int nchan;                  // pairwise feature channels C (Eq. 9); f holds C volumes
     long long fstride;          // elements between consecutive channel volumes of f
+    // specialised kernel, FP32 only: per-voxel terms the adjoint needs, pitched
+    // like the iterate (null = not written): the bracket K = C0 - alpha (f^2 C0
+    // - 2 f C1 + C2) with y = scale * gain * sp * K, and F = f C0 - C1
+    float* aux_k;
+    float* aux_f;
 };
 
 // ---------------------------------------------------------------- storage

@@ -104,6 +104,28 @@ struct AdjParams {
     float gx[2 * kMaxR + 1];
 };
 
+// reverse step on the specialised forward kernel (adjoint.cu)
+struct AdjCombineParams {
+    const float* u;             // u_k (pitched FP32)
+    const float* x_cur;         // stored x^k
+    const float* sp;
+    const float* ku;            // K_U, F_U of the forward kernel run on u_k
+    const float* fu;
+    const float* kx;            // K_X, F_X of the recomputed step k (stored x^k)
+    const float* fx;
+    float* dsp;                 // accumulators (+=)
+    float* df;
+    const double* s_cur;        // x^k = s_cur * stored x^k
+    double* c_out;              // receives x^k . g_k
+    double* partials;           // [blocks]
+    unsigned* counter;          // 0 before the call, 0 after
+    VideoGeom g;
+    float alpha;
+};
+cudaError_t launch_uprep(const float* g_in, const float* x_next, const double* s_next, const double* c,
+                         const double* ny, float* u_out, const VideoGeom& g, int blocks, cudaStream_t s);
+cudaError_t launch_adj_combine(const AdjCombineParams& P, int blocks, cudaStream_t s);
+
 size_t adjoint_smem_bytes(int rt, int ry, int rx);
 cudaError_t setup_adjoint(int rt, int ry, int rx);
 cudaError_t launch_adjoint(const AdjParams& P, int n_items, cudaStream_t s);

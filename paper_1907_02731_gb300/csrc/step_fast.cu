@@ -274,7 +274,7 @@ __device__ __forceinline__ void xpass_abc(const float* row_ab, const float* row_
 // load of frame p + LA (issued at frame p, after A's EMPTY wait) overwrites
 // frame p - RT - 2, whose last reader (B's combine of that frame, at B's
 // frame p - 2) arrived on EMPTY before A passed that wait.
-template <int RT, int RY, int RX, typename TS>
+template <int RT, int RY, int RX, typename TS, bool AUX>
 __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant__ StepParams P) {
     using C = Cfg<RT, RY, RX, TS>;
     constexpr int NR = C::NR, NS = C::NS;
@@ -485,12 +485,23 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     Vec4<TS>::load(reinterpret_cast<const TS*>(st) + off, xs);
                     Vec4<TS>::load(reinterpret_cast<const TS*>(st + C::ARR) + off, sps);
                     Vec4<TS>::load(reinterpret_cast<const TS*>(st + 2 * C::ARR) + off, fs);
+                    float ak[4], af[4];   // adjoint terms (AUX only)
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         // scale and gain applied here; t1 = f C0 - 2 C1
                         const float t1 = fmaf(fs[i], cab[i].x, -2.f * cab[i].y);
                         const float t2 = fmaf(fs[i], t1, c2[i]);
-                        z[i] = (sg_s * sps[i]) * fmaf(-alpha, t2, cab[i].x);
+                        const float kb = fmaf(-alpha, t2, cab[i].x);
+                        z[i] = (sg_s * sps[i]) * kb;
+                        if (AUX) {
+                            ak[i] = kb;
+                            af[i] = t1 + cab[i].y;
+                        }
+                    }
+                    if (AUX && P.aux_k && st_ok && xg < g.pitch) {
+                        const long long ao = g.off + (long long)o * g.plane + (long long)yy * g.pitch + xg;
+                        Vec4<float>::store(P.aux_k + ao, ak);
+                        Vec4<float>::store(P.aux_f + ao, af);
                     }
                     if (st_ok) {
                         if (FO) {
@@ -593,26 +604,29 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 // --------------------------------------------------------------- host side
 struct FastEntry {
     int rt, ry, rx, storage;
+    bool aux;
     const void* fn;
     int smem;
 };
 
 #define SFSEG_FAST(RT, RY, RX)                                                                    \
-    {RT, RY, RX, 0, (const void*)fast::step_fast_kernel<RT, RY, RX, float>,                     \
+    {RT, RY, RX, 0, false, (const void*)fast::step_fast_kernel<RT, RY, RX, float, false>,       \
      fast::Cfg<RT, RY, RX, float>::SMEM},                                                          \
-    {RT, RY, RX, 1, (const void*)fast::step_fast_kernel<RT, RY, RX, __nv_bfloat16>,             \
+    {RT, RY, RX, 1, false, (const void*)fast::step_fast_kernel<RT, RY, RX, __nv_bfloat16, false>, \
      fast::Cfg<RT, RY, RX, __nv_bfloat16>::SMEM},                                                  \
-    {RT, RY, RX, 2, (const void*)fast::step_fast_kernel<RT, RY, RX, __half>,                    \
-     fast::Cfg<RT, RY, RX, __half>::SMEM}
+    {RT, RY, RX, 2, false, (const void*)fast::step_fast_kernel<RT, RY, RX, __half, false>,      \
+     fast::Cfg<RT, RY, RX, __half>::SMEM},                                                         \
+    {RT, RY, RX, 0, true, (const void*)fast::step_fast_kernel<RT, RY, RX, float, true>,         \
+     fast::Cfg<RT, RY, RX, float>::SMEM}
 
 static const FastEntry kFast[] = {
     SFSEG_FAST(2, 5, 5),   // 11x11x5 Gaussian
     SFSEG_FAST(2, 4, 4),   // 9x9x5
 };
 
-static const FastEntry* find_fast(int rt, int ry, int rx, int storage) {
+static const FastEntry* find_fast(int rt, int ry, int rx, int storage, bool aux = false) {
     for (const FastEntry& e : kFast)
-        if (e.rt == rt && e.ry == ry && e.rx == rx && e.storage == storage) return &e;
+        if (e.rt == rt && e.ry == ry && e.rx == rx && e.storage == storage && e.aux == aux) return &e;
     return nullptr;
 }
 
@@ -635,11 +649,15 @@ void fast_box(int ry, int* box_w, int* box_h, int* x_pad) {
 cudaError_t setup_step_fast(int rt, int ry, int rx, int storage) {
     const FastEntry* e = find_fast(rt, ry, rx, storage);
     if (!e) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem);
+    cudaError_t r = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem);
+    const FastEntry* ea = find_fast(rt, ry, rx, storage, true);   // adjoint-terms variant (FP32)
+    if (r == cudaSuccess && ea)
+        r = cudaFuncSetAttribute(ea->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ea->smem);
+    return r;
 }
 
 cudaError_t launch_step_fast(int storage, const StepParams& P, int n_ctas, cudaStream_t s) {
-    const FastEntry* e = find_fast(P.rt, P.ry, P.rx, storage);
+    const FastEntry* e = find_fast(P.rt, P.ry, P.rx, storage, P.aux_k != nullptr);
     if (!e) return cudaErrorInvalidValue;
     void* args[] = {const_cast<StepParams*>(&P)};
     return cudaLaunchKernel(e->fn, dim3(n_ctas), dim3(fast::NT), args, (size_t)e->smem, s);
