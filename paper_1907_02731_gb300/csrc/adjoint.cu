@@ -145,14 +145,8 @@ __global__ void __launch_bounds__(AJ_THREADS) adjoint_kernel(const __grid_consta
 __global__ void __launch_bounds__(256) dot_kernel(const float* x, const double* scale_x, const float* gv,
                                                   VideoGeom g, double* partials, unsigned* counter,
                                                   double* out) {
-    const long long n = g.n, hw = (long long)g.h * g.w;
     float part = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw;
-        const long long o = g.off + t * g.plane + (r / g.w) * g.pitch + (r % g.w);
-        part = fmaf(x[o], gv[o], part);
-    }
+    for_each_voxel(g, [&](long long, long long o) { part = fmaf(x[g.off + o], gv[g.off + o], part); });
     __shared__ double sh[32];
     __shared__ int s_last;
     const float w = warp_sum(part);
@@ -179,15 +173,11 @@ __global__ void __launch_bounds__(256) dot_kernel(const float* x, const double* 
 // device scalar (nullable = 1).
 __global__ void __launch_bounds__(256) pitch_copy_kernel(const float* src, float* dst, VideoGeom g,
                                                          int to_pitched, const double* scale) {
-    const long long n = g.n, hw = (long long)g.h * g.w;
     const float sc = scale ? (float)*scale : 1.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw;
-        const long long o = g.off + t * g.plane + (r / g.w) * g.pitch + (r % g.w);
-        if (to_pitched) dst[o] = src[i] * sc;
-        else dst[i] = src[o] * sc;
-    }
+    for_each_voxel(g, [&](long long i, long long o) {
+        if (to_pitched) dst[g.off + o] = src[i] * sc;
+        else dst[i] = src[g.off + o] * sc;
+    });
 }
 
 // Per-video state for recomputing forward steps from a checkpoint.
@@ -200,34 +190,53 @@ __global__ void __launch_bounds__(256) pitch_copy_kernel(const float* src, float
 // 3. adj_combine: dL/dsp += u K_X s_cur + x K_U, dL/df += -2 alpha sp
 //    (u F_X s_cur + x F_U), x = s_cur * stored x^k, and x^k.g_k for the next
 //    (earlier) step, g_k = sp K_U.
+// Both sweep the whole pitched volume with 16-byte accesses: the pad columns
+// are zero in u, x and sp, so they contribute nothing (pitch is a multiple of
+// 8 and every video starts 256-byte aligned).
 __global__ void __launch_bounds__(256) uprep_kernel(const float* g_in, const float* x_next, const double* s_next,
                                                     const double* c, const double* ny, float* u_out,
                                                     VideoGeom g) {
-    const long long n = g.n, hw = (long long)g.h * g.w;
+    const long long n4 = (long long)g.nf * g.plane / 4;
     const float cs = (float)(*c * *s_next), inv = (float)(1.0 / *ny);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+    const float4* G = reinterpret_cast<const float4*>(g_in + g.off);
+    const float4* X = reinterpret_cast<const float4*>(x_next + g.off);
+    float4* U = reinterpret_cast<float4*>(u_out + g.off);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
-        const long long o = g.off + t * g.plane + yy * g.pitch + xx;
-        u_out[o] = (g_in[o] - cs * x_next[o]) * inv;
+        const float4 a = G[i], b = X[i];
+        U[i] = make_float4((a.x - cs * b.x) * inv, (a.y - cs * b.y) * inv, (a.z - cs * b.z) * inv,
+                           (a.w - cs * b.w) * inv);
     }
 }
 
 __global__ void __launch_bounds__(256) adj_combine_kernel(const __grid_constant__ AdjCombineParams P) {
     const VideoGeom g = P.g;
-    const long long n = g.n, hw = (long long)g.h * g.w;
+    const long long n4 = (long long)g.nf * g.plane / 4;
     const float s_cur = (float)*P.s_cur, m2a = -2.f * P.alpha;
+    auto v4 = [&](const float* p) { return reinterpret_cast<const float4*>(p + g.off); };
+    const float4 *U = v4(P.u), *X = v4(P.x_cur), *S = v4(P.sp), *KU = v4(P.ku), *FU = v4(P.fu),
+                 *KX = v4(P.kx), *FX = v4(P.fx);
+    float4* DS = reinterpret_cast<float4*>(P.dsp + g.off);
+    float4* DF = reinterpret_cast<float4*>(P.df + g.off);
     float part = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
-        const long long o = g.off + t * g.plane + yy * g.pitch + xx;
-        const float u = P.u[o], x = s_cur * P.x_cur[o], s = P.sp[o];
-        const float ku = P.ku[o], fu = P.fu[o];
-        const float kx = s_cur * P.kx[o], fx = s_cur * P.fx[o];
-        P.dsp[o] += fmaf(u, kx, x * ku);
-        P.df[o] += m2a * s * fmaf(u, fx, x * fu);
-        part = fmaf(x, s * ku, part);                 // x^k . g_k, g_k = sp K_U
+        const float4 u4 = U[i], x4 = X[i], s4 = S[i], ku4 = KU[i], fu4 = FU[i], kx4 = KX[i], fx4 = FX[i];
+        float4 ds = DS[i], df = DF[i];
+        const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, xx[4] = {x4.x, x4.y, x4.z, x4.w};
+        const float ss[4] = {s4.x, s4.y, s4.z, s4.w}, kuv[4] = {ku4.x, ku4.y, ku4.z, ku4.w};
+        const float fuv[4] = {fu4.x, fu4.y, fu4.z, fu4.w}, kxv[4] = {kx4.x, kx4.y, kx4.z, kx4.w};
+        const float fxv[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
+        float dsv[4] = {ds.x, ds.y, ds.z, ds.w}, dfv[4] = {df.x, df.y, df.z, df.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float x = s_cur * xx[j];
+            dsv[j] += fmaf(uu[j], s_cur * kxv[j], x * kuv[j]);
+            dfv[j] += m2a * ss[j] * fmaf(uu[j], s_cur * fxv[j], x * fuv[j]);
+            part = fmaf(x, ss[j] * kuv[j], part);          // x^k . g_k, g_k = sp K_U
+        }
+        DS[i] = make_float4(dsv[0], dsv[1], dsv[2], dsv[3]);
+        DF[i] = make_float4(dfv[0], dfv[1], dfv[2], dfv[3]);
     }
     const float w = warp_sum(part);
     __shared__ double sh[32];

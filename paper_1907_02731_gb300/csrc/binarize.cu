@@ -48,13 +48,8 @@ __global__ void __launch_bounds__(256) vmax_stored_kernel(const __grid_constant_
     if (P.state[P.video].done) return;
     const VideoGeom g = P.g;
     const TS* Z = (const TS*)P.buf + g.off;
-    const long long hw = (long long)g.h * g.w;
     float m = -INFINITY;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
-        m = fmaxf(m, to_f(Z[t * g.plane + yy * g.pitch + xx]));
-    }
+    for_each_voxel(g, [&](long long, long long o) { m = fmaxf(m, to_f(Z[o])); });
     m = block_max(m);
     if (threadIdx.x == 0) atomicMax(P.vmax_key, float_key(m));
 }
@@ -63,21 +58,17 @@ template <typename TS>
 __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ ProjectParams P) {
     const VideoGeom g = P.g;
     TS* Z = (TS*)P.buf + g.off;
-    const long long hw = (long long)g.h * g.w;
     const float vmax = key_float(*P.vmax_key);
     float part = 0.f;
     if (!P.state[P.video].done && vmax > 0.f && isfinite(vmax)) {
         const float inv = 1.f / vmax;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.n;
-             i += (long long)gridDim.x * blockDim.x) {
-            const long long t = i / hw, r = i - t * hw, yy = r / g.w, xx = r - yy * g.w;
-            const long long o = t * g.plane + yy * g.pitch + xx;
+        for_each_voxel(g, [&](long long, long long o) {
             const float u = to_f(Z[o]) * inv;
             const TS ps = from_f<TS>(1.f / (1.f + expf(-P.beta * (u - P.tau))));
             Z[o] = ps;
             const float pv = to_f(ps);
             part = fmaf(pv, pv, part);
-        }
+        });
     }
     // FP32 per thread, FP64 per warp and block
     const float w = warp_sum(part);

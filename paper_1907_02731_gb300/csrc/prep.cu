@@ -14,15 +14,10 @@ template <typename TS>
 __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constant__ PrepFeatParams P) {
     const VideoGeom g = P.g;
     const long long n = g.n;
-    const long long hw = (long long)g.h * g.w;
     TS* SPo = (TS*)P.sp_out + g.off;
     TS* Fo = (TS*)P.f_out + g.off;
     int bad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw;
-        const long long yy = r / g.w, xx = r - yy * g.w;
-        const long long o = t * g.plane + yy * g.pitch + xx;
+    for_each_voxel(g, [&](long long i, long long o) {
         const float s = P.s[i];
         const float sp = P.s_is_sp ? s : powf(s, P.p);
         bad |= !isfinite(s) | !isfinite(sp);
@@ -32,28 +27,23 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
             bad |= !isfinite(fv);
             Fo[c * P.chan_stride + o] = from_f<TS>(fv);
         }
-    }
+    });
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.bad, 1);
 }
 
 template <typename TS>
 __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ PrepXParams P) {
     const VideoGeom g = P.g;
-    const long long n = g.n;
-    const long long hw = (long long)g.h * g.w;
     TS* Xo = (TS*)P.x_out + g.off;
     float part = 0.f;
     int bad = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long t = i / hw, r = i - t * hw;
-        const long long yy = r / g.w, xx = r - yy * g.w;
+    for_each_voxel(g, [&](long long i, long long o) {
         const TS xs = from_f<TS>(P.x[i]);
         const float xv = to_f(xs);
         bad |= !isfinite(xv);
-        Xo[t * g.plane + yy * g.pitch + xx] = xs;
+        Xo[o] = xs;
         part = fmaf(xv, xv, part);
-    }
+    });
     bad = __syncthreads_or(bad);
     __shared__ double sh[32];
     __shared__ int s_last;
@@ -102,19 +92,18 @@ template <typename TS>
 __global__ void __launch_bounds__(256) finish_kernel(const __grid_constant__ FinishParams P) {
     const VideoGeom g = P.g;
     const VState st = P.state[P.video];
-    const long long n = g.n, hw = (long long)g.h * g.w;
+    const long long n = g.n;
     const bool in_place = (st.status == 0 && st.iter == P.final_iter);
     const float sc = (float)st.scale;
     const TS* src = (const TS*)((st.iter & 1) ? P.buf1 : P.buf0) + g.off;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (in_place) {
+    if (in_place) {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x)
             P.out[i] = P.out[i] * sc;
-        } else {
-            const long long t = i / hw, r = i - t * hw;
-            const long long yy = r / g.w, xx = r - yy * g.w;
-            P.out[i] = (float)(st.scale * (double)to_f(src[t * g.plane + yy * g.pitch + xx]));
-        }
+    } else {
+        for_each_voxel(g, [&](long long i, long long o) {
+            P.out[i] = (float)(st.scale * (double)to_f(src[o]));
+        });
     }
 }
 

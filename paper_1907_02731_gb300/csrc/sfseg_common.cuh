@@ -111,6 +111,22 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
 }
 template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
 
+// ------------------------------------------------------------ traversal
+// Visits every voxel of one video once: the grid's blocks take the rows
+// r = t h + y in turn and their threads the columns, so the contiguous index
+// (t h + y) w + x and the pitched offset t plane + y pitch + x (without
+// g.off) cost one 32-bit division per row, not two 64-bit ones per voxel.
+template <typename Fn>
+__device__ __forceinline__ void for_each_voxel(const VideoGeom& g, Fn&& fn) {
+    const int rows = g.nf * g.h;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int t = r / g.h, y = r - t * g.h;
+        const long long src = (long long)r * g.w;
+        const long long dst = (long long)t * g.plane + (long long)y * g.pitch;
+        for (int x = threadIdx.x; x < g.w; x += blockDim.x) fn(src + x, dst + x);
+    }
+}
+
 // ------------------------------------------------------------ reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
