@@ -166,6 +166,17 @@ sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* ctx, const float* d_s, con
                                            float* d_x, int32_t n_iters, const sfseg_binarize* b,
                                            uint8_t* d_mask, void* stream);
 
+/* Test aid for failure detection (no counterpart in the paper).  The next
+ * n_steps step launches of this context (specialised step kernel only) make
+ * the first x-pass warp of every CTA wait on a barrier that nothing arrives
+ * on; the wait gives up after its time limit (1 s), the CTA's other waits give
+ * up at once, the loads in flight are drained, and the step reports
+ * SFSEG_ETIMEOUT through the device status (sfseg_sync_status, or the next
+ * synchronising call).  No GPU fault, trap or hang; the context stays usable.
+ * Launches with a pending injection run without a CUDA graph.
+ * Errors: EINVAL, EUNSUPPORTED (context not on the specialised kernel). */
+sfseg_status sfseg_debug_inject_timeout(sfseg_ctx* ctx, int32_t n_steps);
+
 /* Rayleigh quotient lambda = x.Mx / x.x (Eq. 3 read as a Rayleigh quotient)
  * and residual ||Mx - lambda x|| / ||x|| of d_x ([nf][h][w] FP32, device)
  * with the features loaded last.  Synchronises the stream.

@@ -32,7 +32,7 @@ EXPORTS = (
     "sfseg_power_iterate_batched", "sfseg_rayleigh", "sfseg_apply", "sfseg_get_trace",
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
     "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
-    "sfseg_default_binarize", "sfseg_power_iterate_binarized",
+    "sfseg_default_binarize", "sfseg_power_iterate_binarized", "sfseg_debug_inject_timeout",
 )
 
 
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
         "sfseg_plan_segments": (_i32, [_i32, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32),
                                        _i32, ctypes.POINTER(_i32), _i32]),
         "sfseg_default_binarize": (None, [ctypes.POINTER(sfseg_binarize)]),
+        "sfseg_debug_inject_timeout": (_i32, [_vp, _i32]),
         "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
                                                  ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
@@ -338,6 +339,11 @@ class SFSeg:
         sfseg_power_iterate_binarized(self.ctx, ds, df, _dev_f32(x, "x").data_ptr(), iters, b,
                                       mask.data_ptr(), _stream_handle())
         return x, mask
+
+    def debug_inject_timeout(self, n_steps: int = 1):
+        """Test aid: the next n_steps steps give up on a device-side wait and
+        report SFSEG_ETIMEOUT (see include/sfseg.h)."""
+        _check(load_library().sfseg_debug_inject_timeout(self.ctx, n_steps), self.ctx)
 
     def power_iterate_batched(self, s_list, f_list, x_list, iters: int):
         """In place on ``x_list`` (x0 in, x^K out)."""

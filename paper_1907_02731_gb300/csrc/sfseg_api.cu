@@ -63,6 +63,8 @@ struct sfseg_ctx {
     unsigned char* d_bin = nullptr;
     // reverse step on the specialised kernel: scratch state, constants, partials
     unsigned char* d_adj_misc = nullptr;
+    // test aid: step launches still to run with an injected device-side timeout
+    int inject_steps = 0;
     void* d_adj = nullptr;      // [C + 4] volumes: recompute ring, g ping-pong, dsp, df
     int adj_cap = 0;
     double* d_adjc = nullptr;   // [2] dot products
@@ -517,6 +519,10 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
 static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s,
                                bool record = false) {
     StepParams P = step_params(c, k, final_out, store, record);
+    if (c->inject_steps > 0) {
+        P.inject_timeout = 1;
+        c->inject_steps -= 1;
+    }
     c->launches += 1;
     if (c->fast) return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
     return launch_step_generic(c->prm.storage, P, c->n_items, s);
@@ -527,7 +533,7 @@ static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, 
 // caller's stream.
 static sfseg_status run_steps(sfseg_ctx* c, int n, cudaStream_t s) {
     if (n <= 0) return SFSEG_OK;
-    if (c->prm.flags & SFSEG_NO_GRAPH) {
+    if ((c->prm.flags & SFSEG_NO_GRAPH) || c->inject_steps > 0) {   // an injection is never captured
         for (int k = 0; k < n; ++k) CUDA_OR(c, launch_step(c, k, false, true, s));
         return SFSEG_OK;
     }
@@ -599,6 +605,9 @@ static sfseg_status prep_x(sfseg_ctx* c, int v, const float* d_x, bool raw, doub
     P.state = c->d_state;
     P.partials = c->d_prep_partials;
     P.counter = c->d_prep_counter;
+    // a step whose CTAs gave up (SFSEG_ETIMEOUT) left its arrival count
+    // unfinished: every call starts the video's count from zero
+    CUDA_OR(c, cudaMemsetAsync(c->d_counters + v, 0, sizeof(unsigned), s));
     CUDA_OR(c, launch_prep_x(c->prm.storage, P, prep_x_blocks(c->geo[v].n), s));
     c->launches += 1;
     return SFSEG_OK;
@@ -1170,6 +1179,14 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
     if (d_gf) CUDA_OR(c, launch_pitch_copy(df, d_gf, g, 0, nullptr, s));
     c->launches += 3;
     c->last_stream = s;
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_debug_inject_timeout(sfseg_ctx* c, int32_t n_steps) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (n_steps < 0) return fail(c, SFSEG_EINVAL, "n_steps must be >= 0");
+    if (!c->fast) return fail(c, SFSEG_EUNSUPPORTED, "timeouts exist only in the specialised step kernel");
+    c->inject_steps = n_steps;
     return SFSEG_OK;
 }
 

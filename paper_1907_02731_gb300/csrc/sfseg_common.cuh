@@ -97,6 +97,9 @@ struct StepParams {
     // - 2 f C1 + C2) with y = scale * gain * sp * K, and F = f C0 - C1
     float* aux_k;
     float* aux_f;
+    // test aid (sfseg_debug_inject_timeout): the first x-pass warp of every CTA
+    // waits once on a barrier nothing arrives on, so the step gives up
+    int inject_timeout;
 };
 
 // ---------------------------------------------------------------- storage

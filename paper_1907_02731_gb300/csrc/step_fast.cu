@@ -45,7 +45,7 @@ constexpr int TX = 112, TY = 12, XPAD = 8, BOXW = TX + 2 * XPAD, YBW = BOXW;
 constexpr int NA_WARPS = 4;                   // warps running the loads and the y-pass
 constexpr int NT = 32 * (NA_WARPS + TY);      // plus one x-pass/combine warp per tile row
 constexpr int LA = 1;                         // frames of TMA lookahead
-constexpr long kWaitTries = 1L << 24;         // bounded mbarrier wait
+constexpr unsigned long long kWaitNs = 1000000000ull;   // a device-side wait gives up after 1 s
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -70,10 +70,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-    for (long i = 0; i < kWaitTries; ++i)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of `parity` to complete, for at most kWaitNs; with an
+// abort flag, also give up as soon as another warp of the CTA has raised it.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* abort = nullptr) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (abort && *abort) return false;
+        if ((i & 63u) == 63u && global_ns() - t0 > kWaitNs) return false;
+    }
 }
 __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap* map, unsigned bar,
                                             int x, int y, int z) {
@@ -284,6 +294,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + NS * C::STAGE + 2 * C::YB);
     __shared__ float s_scale, s_gain, s_shift;
     __shared__ int s_skip, s_abort;
+    __shared__ __align__(8) unsigned long long s_never;   // an mbarrier nothing arrives on (fault injection)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool is_a = warp < NA_WARPS;
@@ -298,9 +309,17 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             mbar_init(smem_u32(&full[b]), NA_WARPS);
             mbar_init(smem_u32(&empty[b]), NB_WARPS);
         }
+        mbar_init(smem_u32(&s_never), 1);
         fence_mbar_init();
         s_abort = 0;
     }
+    // a wait that gave up: the step fails with SFSEG_ETIMEOUT and every other
+    // wait of the CTA gives up at once (the loads in flight are still drained)
+    auto give_up = [&](int v) {
+        s_abort = 1;
+        atomicExch(&P.state[v].status, 6);
+        P.state[v].done = 1;
+    };
     __syncthreads();
     // bit b: parity of the first FULL / EMPTY completion of buffer b in the
     // current segment; use n of buffer b completes phase base ^ (n & 1)
@@ -370,15 +389,12 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                 const int p = p_first + vc;
                 const int b = vc & 1;
                 const unsigned n = (unsigned)(vc >> 1);
-                if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u)) s_abort = 1;
-                if (tid == 0 && vc + LA < n_valid) issue(p + LA);
+                if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u, &s_abort))
+                    give_up(v);
+                if (tid == 0 && !s_abort && vc + LA < n_valid) issue(p + LA);
                 const int s = p % NS;
-                if (!mbar_wait(smem_u32(&bars[s]), parity(p))) {
-                    s_abort = 1;
-                    atomicExch(&P.state[v].status, 6);
-                    P.state[v].done = 1;
-                }
-                owed &= ~(1u << s);
+                if (mbar_wait(smem_u32(&bars[s]), parity(p), &s_abort)) owed &= ~(1u << s);
+                else give_up(v);   // the load stays owed: drained before the CTA leaves
                 if (a_task) {
                     const unsigned char* st = stages + s * C::STAGE;
                     const int r0 = a_h * C::TROWS;
@@ -454,8 +470,11 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                 float2 pab[4];
                 float pc[4];
                 if (valid) {
-                    if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ (unsigned)(vc >> 1)) & 1u))
-                        s_abort = 1;
+                    if (P.inject_timeout && brow == 0 && vc == 0 &&
+                        !mbar_wait(smem_u32(&s_never), 0u, &s_abort))
+                        give_up(v);
+                    if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ (unsigned)(vc >> 1)) & 1u, &s_abort))
+                        give_up(v);
                     const float* yc = yb + b * 3 * TY * YBW;
                     // lanes 28..31 have no outputs: give them lane 27's window so
                     // every read stays inside the row
@@ -559,7 +578,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
         }
         __syncthreads();
         if (s_abort) {
-            // wait (bounded) for loads still in flight into this CTA's stages
+            // wait (bounded, ignoring the abort flag) for loads still in flight
+            // into this CTA's stages
             if (tid == 0)
                 for (int s = 0; s < NS; ++s)
                     if (owed & (1u << s)) (void)mbar_wait(smem_u32(&bars[s]), (owed_par >> s) & 1u);

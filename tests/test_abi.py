@@ -84,3 +84,7 @@ def test_noalloc_rejects_channels(lib):
     with pytest.raises(sf.SFSegError) as ei:
         sf.sfseg_power_iterate_noalloc(p, 1, 1, 1, 3)
     assert ei.value.status == sf.SFSEG_EUNSUPPORTED
+
+
+def test_debug_injection_null_context(lib):
+    assert lib.sfseg_debug_inject_timeout(None, 1) == sf.SFSEG_EINVAL
