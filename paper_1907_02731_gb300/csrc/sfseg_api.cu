@@ -12,8 +12,16 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sfseg.h"
 #include "sfseg_launch.h"
+
+// NVTX range around a public entry point (a no-op unless a profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 using namespace sfseg;
 
@@ -787,6 +795,7 @@ void sfseg_destroy(sfseg_ctx* ctx) {
 }
 
 sfseg_status sfseg_load_features(sfseg_ctx* c, const float* d_s, const float* d_f, void* stream) {
+    NvtxRange nvtx_range("sfseg_load_features");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (c->batched) return fail(c, SFSEG_EINVAL, "batched context: use sfseg_load_features_batched");
     return load_features_impl(c, &d_s, &d_f, (cudaStream_t)stream);
@@ -794,6 +803,7 @@ sfseg_status sfseg_load_features(sfseg_ctx* c, const float* d_s, const float* d_
 
 sfseg_status sfseg_load_features_batched(sfseg_ctx* c, const float* const* d_s,
                                          const float* const* d_f, void* stream) {
+    NvtxRange nvtx_range("sfseg_load_features_batched");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (!d_s || !d_f) return fail(c, SFSEG_EINVAL, "NULL pointer array");
     return load_features_impl(c, d_s, d_f, (cudaStream_t)stream);
@@ -801,6 +811,7 @@ sfseg_status sfseg_load_features_batched(sfseg_ctx* c, const float* const* d_s,
 
 sfseg_status sfseg_power_iterate(sfseg_ctx* c, const float* d_s, const float* d_f, float* d_x,
                                  int32_t n_iters, double tol, int32_t* iters_done, void* stream) {
+    NvtxRange nvtx_range("sfseg_power_iterate");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (c->batched) return fail(c, SFSEG_EINVAL, "batched context: use sfseg_power_iterate_batched");
     cudaStream_t s = (cudaStream_t)stream;
@@ -828,6 +839,7 @@ static constexpr int kBinBlocks = 1216;   // 8 blocks of 256 threads per SM on 1
 sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* c, const float* d_s, const float* d_f,
                                            float* d_x, int32_t n_iters, const sfseg_binarize* b,
                                            uint8_t* d_mask, void* stream) {
+    NvtxRange nvtx_range("sfseg_power_iterate_binarized");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (c->batched) return fail(c, SFSEG_EINVAL, "binarisation takes a single-video context");
     if (!b) return fail(c, SFSEG_EINVAL, "schedule is NULL");
@@ -905,6 +917,7 @@ sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* c, const float* d_s, const
 sfseg_status sfseg_power_iterate_batched(sfseg_ctx* c, const float* const* d_s,
                                          const float* const* d_f, float* const* d_x,
                                          int32_t n_iters, void* stream) {
+    NvtxRange nvtx_range("sfseg_power_iterate_batched");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -920,6 +933,7 @@ sfseg_status sfseg_power_iterate_batched(sfseg_ctx* c, const float* const* d_s,
 
 sfseg_status sfseg_rayleigh(sfseg_ctx* c, const float* d_x, double* lambda, double* residual,
                             void* stream) {
+    NvtxRange nvtx_range("sfseg_rayleigh");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (c->batched) return fail(c, SFSEG_EINVAL, "rayleigh needs a single-video context");
     if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
@@ -941,6 +955,7 @@ sfseg_status sfseg_rayleigh(sfseg_ctx* c, const float* d_x, double* lambda, doub
 }
 
 sfseg_status sfseg_apply(sfseg_ctx* c, const float* d_x, float* d_y, void* stream) {
+    NvtxRange nvtx_range("sfseg_apply");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (c->batched) return fail(c, SFSEG_EINVAL, "apply needs a single-video context");
     if (!d_x || !d_y) return fail(c, SFSEG_EINVAL, "NULL pointer");
@@ -994,6 +1009,7 @@ int32_t sfseg_get_trace(sfseg_ctx* c, int32_t video, double* rayleigh, double* r
 
 sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float* d_gf,
                            float* d_gx0, void* stream) {
+    NvtxRange nvtx_range("sfseg_adjoint");
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (!d_gx) return fail(c, SFSEG_EINVAL, "d_gx is NULL");
     if (!c->recorded) return fail(c, SFSEG_ESTATE, "no recorded forward (create with SFSEG_RECORD)");
