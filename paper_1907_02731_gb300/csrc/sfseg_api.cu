@@ -271,16 +271,18 @@ static const char* encode_maps(sfseg_ctx* c, CUtensorMap* maps) {
     const CUtensorMapDataType dt = c->prm.storage == SFSEG_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->prm.storage == SFSEG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    void* arrays[4] = {c->sp, c->f, c->xa, c->xb};
+    void* arrays[kMapsPerVideo] = {c->sp, c->f, c->xa, c->xb};
+    for (int ch = 1; ch < c->prm.nchan; ++ch) arrays[3 + ch] = (char*)c->f + (size_t)ch * c->total * c->elt;
+    const int n_arrays = 3 + c->prm.nchan;
     for (int v = 0; v < c->nv; ++v) {
         const VideoGeom& g = c->geo[v];
         cuuint64_t gdim[3] = {(cuuint64_t)g.w, (cuuint64_t)g.h, (cuuint64_t)g.nf};
         cuuint64_t gstr[2] = {(cuuint64_t)g.pitch * c->elt, (cuuint64_t)g.plane * c->elt};
         cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1u};
         cuuint32_t est[3] = {1u, 1u, 1u};
-        for (int a = 0; a < 4; ++a) {
+        for (int a = 0; a < n_arrays; ++a) {
             void* base = (char*)arrays[a] + (size_t)g.off * c->elt;
-            CUresult r = enc(&maps[4 * v + a], dt, 3, base, gdim, gstr, box, est,
+            CUresult r = enc(&maps[kMapsPerVideo * v + a], dt, 3, base, gdim, gstr, box, est,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
             if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed";
@@ -319,7 +321,8 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         off += (g.nf * g.plane + align - 1) / align * align;
         c->geo.push_back(g);
     }
-    c->fast = !(prm->flags & SFSEG_GENERIC) && prm->nchan == 1 &&
+    // several channels run as one pass per channel, with FP32 partial sums
+    c->fast = !(prm->flags & SFSEG_GENERIC) && (prm->nchan == 1 || prm->storage == SFSEG_F32) &&
               fast_available(prm->rt, prm->ry, prm->rx, prm->storage);
     std::vector<WorkItem> items;
     std::vector<int> cta_begin, vseg;
@@ -410,7 +413,7 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
     if (c->fast) {
         ALLOC(c->d_cta_begin, sizeof(int) * cta_begin.size());
         ALLOC(c->d_vseg, sizeof(int) * (vseg.size() + 1));
-        ALLOC(c->d_maps, sizeof(CUtensorMap) * 4 * nv);
+        ALLOC(c->d_maps, sizeof(CUtensorMap) * kMapsPerVideo * nv);
     }
 #undef ALLOC
     cudaError_t e = cudaSuccess;
@@ -443,7 +446,7 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         if (e == cudaSuccess && !vseg.empty())
             e = cudaMemcpy(c->d_vseg, vseg.data(), sizeof(int) * vseg.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) {
-            std::vector<CUtensorMap> maps(4 * (size_t)nv);
+            std::vector<CUtensorMap> maps(kMapsPerVideo * (size_t)nv);
             const char* why = encode_maps(c, maps.data());
             if (why) {
                 fail(nullptr, SFSEG_ECUDA, "tensor map: %s", why);
@@ -532,6 +535,28 @@ static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, 
         c->inject_steps -= 1;
     }
     c->launches += 1;
+    if (c->fast && c->prm.nchan > 1) {
+        // Eq. 9 as one pass per channel: every pass adds its M_c x to the
+        // partial sum in the step's output buffer; the last pass also reduces
+        // (and writes the caller's buffer in final mode)
+        void* zbuf = (k & 1) ? c->xa : c->xb;
+        const int C = c->prm.nchan;
+        for (int ch = 0; ch < C; ++ch) {
+            StepParams Q = P;
+            Q.f_chan = ch;
+            Q.acc_in = ch > 0 ? zbuf : nullptr;
+            Q.no_reduce = ch < C - 1 ? 1 : 0;
+            if (ch < C - 1) {
+                Q.z_out = zbuf;
+                Q.final_out = nullptr;
+            }
+            if (ch < C - 1 && Q.inject_timeout) Q.inject_timeout = 0;
+            cudaError_t e = launch_step_fast(c->prm.storage, Q, c->n_ctas, s);
+            if (e != cudaSuccess) return e;
+        }
+        c->launches += C - 1;
+        return cudaSuccess;
+    }
     if (c->fast) return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
     return launch_step_generic(c->prm.storage, P, c->n_items, s);
 }

@@ -22,6 +22,8 @@ constexpr int kMaxRt = 8;       // largest temporal radius
 constexpr int kRed = 4;         // reductions per step: z.z, xh.z, xh.xh, |z - s xh|^2
 constexpr int kMaxDynSmem = 232448;   // dynamic shared memory per block (227 KB)
 constexpr int kMaxChan = 4;           // pairwise feature channels (Eq. 9) of the step kernels
+// TMA descriptors per video: sp, f channel 0, x_a, x_b, f channels 1 .. kMaxChan - 1
+constexpr int kMapsPerVideo = 3 + kMaxChan;
 
 // Per-step record of the forward pass for the adjoint (per video, nullable):
 // scale[k] turns the stored iterate of step k into the unit-norm x^k (k = 0..K),
@@ -100,6 +102,13 @@ struct StepParams {
     // test aid (sfseg_debug_inject_timeout): the first x-pass warp of every CTA
     // waits once on a barrier nothing arrives on, so the step gives up
     int inject_timeout;
+    // specialised kernel, several channels (Eq. 9) as one pass per channel:
+    // the pass reads channel f_chan; acc_in (or null) holds the partial sum of
+    // the earlier passes, added before the store; no_reduce skips the
+    // reductions and the arrival (every pass but the last)
+    int f_chan;
+    const void* acc_in;
+    int no_reduce;
 };
 
 // ---------------------------------------------------------------- storage

@@ -284,7 +284,7 @@ __device__ __forceinline__ void xpass_abc(const float* row_ab, const float* row_
 // load of frame p + LA (issued at frame p, after A's EMPTY wait) overwrites
 // frame p - RT - 2, whose last reader (B's combine of that frame, at B's
 // frame p - 2) arrived on EMPTY before A passed that wait.
-template <int RT, int RY, int RX, typename TS, bool AUX>
+template <int RT, int RY, int RX, typename TS, bool AUX, bool MC>
 __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant__ StepParams P) {
     using C = Cfg<RT, RY, RX, TS>;
     constexpr int NR = C::NR, NS = C::NS;
@@ -365,9 +365,9 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 
         if (is_a) {
             // ============================ A: loads + y-pass ====================
-            const CUtensorMap* map_sp = maps + 4 * v + 0;
-            const CUtensorMap* map_f = maps + 4 * v + 1;
-            const CUtensorMap* map_x = maps + 4 * v + 2 + P.x_sel;
+            const CUtensorMap* map_sp = maps + kMapsPerVideo * v + 0;
+            const CUtensorMap* map_f = maps + kMapsPerVideo * v + ((!MC || P.f_chan == 0) ? 1 : 3 + P.f_chan);
+            const CUtensorMap* map_x = maps + kMapsPerVideo * v + 2 + P.x_sel;
             auto issue = [&](int p) {
                 const int s = p % NS;
                 const unsigned bar = smem_u32(&bars[s]);
@@ -517,6 +517,14 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                             af[i] = t1 + cab[i].y;
                         }
                     }
+                    if (MC && P.acc_in && st_ok && xg < g.pitch) {   // earlier channels' passes (Eq. 9 sums them)
+                        float zp[4];
+                        Vec4<TS>::load((const TS*)P.acc_in + g.off + (long long)o * g.plane +
+                                           (long long)yy * g.pitch + xg,
+                                       zp);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) z[i] += zp[i];
+                    }
                     if (AUX && P.aux_k && st_ok && xg < g.pitch) {
                         const long long ao = g.off + (long long)o * g.plane + (long long)yy * g.pitch + xg;
                         Vec4<float>::store(P.aux_k + ao, ak);
@@ -535,7 +543,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                             Vec4<TS>::store(Z + (long long)o * g.plane + (long long)yy * g.pitch + xg, z);
                         }
                     }
-                    if (out_lane) {
+                    if (out_lane && !(MC && P.no_reduce)) {
 #pragma unroll
                         for (int i = 0; i < 4; ++i) {
                             part[0] = fmaf(z[i], z[i], part[0]);
@@ -598,7 +606,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const int cnt = (j < n_valid) ? (n_valid - 1 - j) / NS + 1 : 0;
             segphase ^= (unsigned)(cnt & 1) << s;
         }
-        if (sg + 1 == seg_e || P.items[sg + 1].video != v) {
+        if (!(MC && P.no_reduce) && (sg + 1 == seg_e || P.items[sg + 1].video != v)) {
             // end of the run: its sum goes to the slot of its last segment, the
             // other segments' slots get zeros, and the run arrives once
             const double sc = (double)s_scale;
@@ -624,19 +632,23 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 // --------------------------------------------------------------- host side
 struct FastEntry {
     int rt, ry, rx, storage;
-    bool aux;
+    bool aux, mc;
     const void* fn;
     int smem;
 };
 
-#define SFSEG_FAST(RT, RY, RX)                                                                    \
-    {RT, RY, RX, 0, false, (const void*)fast::step_fast_kernel<RT, RY, RX, float, false>,       \
-     fast::Cfg<RT, RY, RX, float>::SMEM},                                                          \
-    {RT, RY, RX, 1, false, (const void*)fast::step_fast_kernel<RT, RY, RX, __nv_bfloat16, false>, \
-     fast::Cfg<RT, RY, RX, __nv_bfloat16>::SMEM},                                                  \
-    {RT, RY, RX, 2, false, (const void*)fast::step_fast_kernel<RT, RY, RX, __half, false>,      \
-     fast::Cfg<RT, RY, RX, __half>::SMEM},                                                         \
-    {RT, RY, RX, 0, true, (const void*)fast::step_fast_kernel<RT, RY, RX, float, true>,         \
+// per radii: FP32 / BF16 / FP16; FP32 with the adjoint terms; FP32 channel passes
+#define SFSEG_FAST(RT, RY, RX)                                                                         \
+    {RT, RY, RX, 0, false, false, (const void*)fast::step_fast_kernel<RT, RY, RX, float, false, false>, \
+     fast::Cfg<RT, RY, RX, float>::SMEM},                                                               \
+    {RT, RY, RX, 1, false, false,                                                                       \
+     (const void*)fast::step_fast_kernel<RT, RY, RX, __nv_bfloat16, false, false>,                      \
+     fast::Cfg<RT, RY, RX, __nv_bfloat16>::SMEM},                                                       \
+    {RT, RY, RX, 2, false, false, (const void*)fast::step_fast_kernel<RT, RY, RX, __half, false, false>, \
+     fast::Cfg<RT, RY, RX, __half>::SMEM},                                                              \
+    {RT, RY, RX, 0, true, false, (const void*)fast::step_fast_kernel<RT, RY, RX, float, true, false>,   \
+     fast::Cfg<RT, RY, RX, float>::SMEM},                                                               \
+    {RT, RY, RX, 0, false, true, (const void*)fast::step_fast_kernel<RT, RY, RX, float, false, true>,   \
      fast::Cfg<RT, RY, RX, float>::SMEM}
 
 static const FastEntry kFast[] = {
@@ -644,9 +656,10 @@ static const FastEntry kFast[] = {
     SFSEG_FAST(2, 4, 4),   // 9x9x5
 };
 
-static const FastEntry* find_fast(int rt, int ry, int rx, int storage, bool aux = false) {
+static const FastEntry* find_fast(int rt, int ry, int rx, int storage, bool aux = false, bool mc = false) {
     for (const FastEntry& e : kFast)
-        if (e.rt == rt && e.ry == ry && e.rx == rx && e.storage == storage && e.aux == aux) return &e;
+        if (e.rt == rt && e.ry == ry && e.rx == rx && e.storage == storage && e.aux == aux && e.mc == mc)
+            return &e;
     return nullptr;
 }
 
@@ -670,14 +683,17 @@ cudaError_t setup_step_fast(int rt, int ry, int rx, int storage) {
     const FastEntry* e = find_fast(rt, ry, rx, storage);
     if (!e) return cudaErrorInvalidValue;
     cudaError_t r = cudaFuncSetAttribute(e->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, e->smem);
-    const FastEntry* ea = find_fast(rt, ry, rx, storage, true);   // adjoint-terms variant (FP32)
+    const FastEntry* ea = find_fast(rt, ry, rx, storage, true);          // adjoint terms (FP32)
     if (r == cudaSuccess && ea)
         r = cudaFuncSetAttribute(ea->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ea->smem);
+    const FastEntry* em = find_fast(rt, ry, rx, storage, false, true);   // channel passes (FP32)
+    if (r == cudaSuccess && em)
+        r = cudaFuncSetAttribute(em->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, em->smem);
     return r;
 }
 
 cudaError_t launch_step_fast(int storage, const StepParams& P, int n_ctas, cudaStream_t s) {
-    const FastEntry* e = find_fast(P.rt, P.ry, P.rx, storage, P.aux_k != nullptr);
+    const FastEntry* e = find_fast(P.rt, P.ry, P.rx, storage, P.aux_k != nullptr, P.nchan > 1);
     if (!e) return cudaErrorInvalidValue;
     void* args[] = {const_cast<StepParams*>(&P)};
     return cudaLaunchKernel(e->fn, dim3(n_ctas), dim3(fast::NT), args, (size_t)e->smem, s);

@@ -157,3 +157,25 @@ def test_fullsize_low_precision_fifty_steps(cuda_device, video, storage):
         eng.close()
     torch.cuda.synchronize()
     assert rel_l2(out[storage], out["f32"]) < TOL_LOWP
+
+
+def test_fullsize_two_channels_sampled_one_step(cuda_device):
+    """Eq. 9 with the 2-channel workload (854x480x72, S = channel 0): y = M S
+    at 4096 sampled voxels plus corners and edges against the oracle's
+    per-voxel routine over both channels."""
+    wl2 = inputs.WORKLOADS["video2ch_72x480x854"]
+    s, f2 = inputs.workload_features(wl2.name)
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=wl2.alpha, p=wl2.p, nchan=2)
+    ds = to_dev(s)
+    eng.load_features(ds, to_dev(f2))
+    y = eng.apply(ds).cpu().numpy().ravel()
+    eng.close()
+    rng = np.random.default_rng(23)
+    nf, h, w = SHAPE
+    pts = [(t, yy, xx) for t in (0, nf - 1) for yy in (0, h // 2, h - 1) for xx in (0, 31, w // 2, w - 1)]
+    idx = np.concatenate([rng.integers(0, s.size, 4096),
+                          np.array([(t * h + yy) * w + xx for t, yy, xx in pts])])
+    sp = oracle.unary(s, wl2.p)
+    ref = oracle.apply_M_at(sp, f2.astype(np.float64), s, RADII, SIG, wl2.alpha, idx)
+    assert rel_l2(y[idx], ref) < 1e-6
+    assert np.max(np.abs(y[idx] - ref) / np.abs(ref).max()) < 1e-6

@@ -118,3 +118,30 @@ def test_multichannel_batched_matches_single(cuda_device):
     for (s, f), d, xb in zip(feats, dims, xs):
         x1, _, _ = _gpu(d, s, f, s, K, radii, sig, 1.0, 0.1, nchan=2)
         assert rel_l2(xb.cpu().numpy(), x1) < 1e-6
+
+
+@pytest.mark.parametrize("C,radii,sig", [(2, (2, 5, 5), (1.5, 3.0, 3.0)), (3, (2, 4, 4), (1.5, 2.5, 2.5))])
+def test_channel_passes_match_any_radius_kernel(cuda_device, C, radii, sig):
+    """FP32 storage runs several channels as one specialised pass per channel
+    (Eq. 9 as a sum); it must agree with the any-radius kernel's C + 2
+    convolutions: iterates, Rayleigh trace, y = Mx and sfseg_rayleigh."""
+    import torch
+    shape, K = (9, 50, 130), 12
+    s, f = _features(shape, C, 4242 + C)
+    outs = []
+    for flags in (0, sf.SFSEG_GENERIC):
+        eng = sf.SFSeg(shape, radii=radii, sigmas=sig, alpha=0.9, p=0.1, nchan=C, flags=flags)
+        try:
+            x = eng.power_iterate(to_dev(s), to_dev(f), to_dev(s), K)
+            torch.cuda.synchronize()
+            tr = eng.trace()
+            y = eng.apply(to_dev(s))
+            lam, res = eng.rayleigh(to_dev(s))
+            outs.append((x.cpu().numpy(), tr, y.cpu().numpy(), lam, res))
+        finally:
+            eng.close()
+    (x1, t1, y1, l1, r1), (x2, t2, y2, l2, r2) = outs
+    assert rel_l2(x1, x2) < 1e-6
+    np.testing.assert_allclose(t1["rayleigh"], t2["rayleigh"], rtol=1e-6)
+    assert rel_l2(y1, y2) < 1e-6
+    assert abs(l1 - l2) < 1e-6 * abs(l2)
