@@ -48,7 +48,7 @@ typedef enum {
     SFSEG_EZERONORM = 4,     /* ||M x|| = 0 at some step (x0 orthogonal to the support) */
     SFSEG_ENONFINITE = 5,    /* NaN/Inf in the inputs or in a norm */
     SFSEG_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-    SFSEG_EUNSUPPORTED = 7,  /* valid request this build does not implement */
+    SFSEG_EUNSUPPORTED = 7,  /* valid request the library does not implement */
     SFSEG_ESTATE = 8         /* call order (e.g. adjoint without a recorded forward) */
 } sfseg_status;
 

@@ -261,7 +261,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// One 3D tiled descriptor per (video, array): dims (w, h, nf) so the box
+// One 3D tiled descriptor per (video, array): dims (w, h, nf) so the TMA box
 // reads zeros outside the volume, row/plane strides of the pitched layout.
 static const char* encode_maps(sfseg_ctx* c, CUtensorMap* maps) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
