@@ -17,17 +17,32 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
     TS* SPo = (TS*)P.sp_out + g.off;
     TS* Fo = (TS*)P.f_out + g.off;
     int bad = 0;
-    for_each_voxel(g, [&](long long i, long long o) {
-        const float s = P.s[i];
-        const float sp = P.s_is_sp ? s : powf(s, P.p);
-        bad |= !isfinite(s) | !isfinite(sp);
-        SPo[o] = from_f<TS>(sp);
-        for (int c = 0; c < P.nchan; ++c) {
-            const float fv = P.f[c * n + i];
-            bad |= !isfinite(fv);
-            Fo[c * P.chan_stride + o] = from_f<TS>(fv);
-        }
-    });
+    const bool pairs = aligned8(P.s) && aligned8(P.f) && (n % 2 == 0);
+    for_each_voxel_pair(
+        g, pairs,
+        [&](long long i, long long o) {
+            const float2 s = *reinterpret_cast<const float2*>(P.s + i);
+            const float sp0 = P.s_is_sp ? s.x : powf(s.x, P.p);
+            const float sp1 = P.s_is_sp ? s.y : powf(s.y, P.p);
+            bad |= !isfinite(s.x) | !isfinite(s.y) | !isfinite(sp0) | !isfinite(sp1);
+            store_pair<TS>(SPo + o, sp0, sp1);
+            for (int c = 0; c < P.nchan; ++c) {
+                const float2 fv = *reinterpret_cast<const float2*>(P.f + c * n + i);
+                bad |= !isfinite(fv.x) | !isfinite(fv.y);
+                store_pair<TS>(Fo + c * P.chan_stride + o, fv.x, fv.y);
+            }
+        },
+        [&](long long i, long long o) {
+            const float s = P.s[i];
+            const float sp = P.s_is_sp ? s : powf(s, P.p);
+            bad |= !isfinite(s) | !isfinite(sp);
+            SPo[o] = from_f<TS>(sp);
+            for (int c = 0; c < P.nchan; ++c) {
+                const float fv = P.f[c * n + i];
+                bad |= !isfinite(fv);
+                Fo[c * P.chan_stride + o] = from_f<TS>(fv);
+            }
+        });
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.bad, 1);
 }
 
@@ -37,13 +52,23 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
     TS* Xo = (TS*)P.x_out + g.off;
     float part = 0.f;
     int bad = 0;
-    for_each_voxel(g, [&](long long i, long long o) {
-        const TS xs = from_f<TS>(P.x[i]);
-        const float xv = to_f(xs);
-        bad |= !isfinite(xv);
-        Xo[o] = xs;
-        part = fmaf(xv, xv, part);
-    });
+    for_each_voxel_pair(
+        g, aligned8(P.x),
+        [&](long long i, long long o) {
+            const float2 xv = *reinterpret_cast<const float2*>(P.x + i);
+            const float x0 = to_f(from_f<TS>(xv.x)), x1 = to_f(from_f<TS>(xv.y));   // as stored
+            bad |= !isfinite(x0) | !isfinite(x1);
+            store_pair<TS>(Xo + o, xv.x, xv.y);
+            part = fmaf(x0, x0, part);
+            part = fmaf(x1, x1, part);
+        },
+        [&](long long i, long long o) {
+            const TS xs = from_f<TS>(P.x[i]);
+            const float xv = to_f(xs);
+            bad |= !isfinite(xv);
+            Xo[o] = xs;
+            part = fmaf(xv, xv, part);
+        });
     bad = __syncthreads_or(bad);
     __shared__ double sh[32];
     __shared__ int s_last;
@@ -97,13 +122,27 @@ __global__ void __launch_bounds__(256) finish_kernel(const __grid_constant__ Fin
     const float sc = (float)st.scale;
     const TS* src = (const TS*)((st.iter & 1) ? P.buf1 : P.buf0) + g.off;
     if (in_place) {
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+        const bool vec = ((unsigned long long)P.out & 15ull) == 0;
+        const long long n4 = vec ? n / 4 : 0;
+        float4* o4 = reinterpret_cast<float4*>(P.out);
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+             i += (long long)gridDim.x * blockDim.x) {
+            float4 v = o4[i];
+            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+            o4[i] = v;
+        }
+        for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x)
             P.out[i] = P.out[i] * sc;
     } else {
-        for_each_voxel(g, [&](long long i, long long o) {
-            P.out[i] = (float)(st.scale * (double)to_f(src[o]));
-        });
+        for_each_voxel_pair(
+            g, aligned8(P.out),
+            [&](long long i, long long o) {
+                const float2 v = load_pair<TS>(src + o);
+                *reinterpret_cast<float2*>(P.out + i) =
+                    make_float2((float)(st.scale * (double)v.x), (float)(st.scale * (double)v.y));
+            },
+            [&](long long i, long long o) { P.out[i] = (float)(st.scale * (double)to_f(src[o])); });
     }
 }
 

@@ -139,6 +139,49 @@ __device__ __forceinline__ void for_each_voxel(const VideoGeom& g, Fn&& fn) {
     }
 }
 
+// The same visit two columns at a time when the rows hold an even number of
+// voxels and the caller's arrays are 8-byte aligned: (i, i + 1) and
+// (o, o + 1) are then aligned pairs (pitch is a multiple of 8, every video
+// 256-byte aligned).  fn2(i, o) handles a pair; otherwise fn1 runs per voxel.
+template <typename Fn2, typename Fn1>
+__device__ __forceinline__ void for_each_voxel_pair(const VideoGeom& g, bool pairs_ok, Fn2&& fn2, Fn1&& fn1) {
+    if (!pairs_ok || (g.w & 1)) {
+        for_each_voxel(g, fn1);
+        return;
+    }
+    const int rows = g.nf * g.h, half_w = g.w >> 1;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int t = r / g.h, y = r - t * g.h;
+        const long long src = (long long)r * g.w;
+        const long long dst = (long long)t * g.plane + (long long)y * g.pitch;
+        for (int x2 = threadIdx.x; x2 < half_w; x2 += blockDim.x) fn2(src + 2 * x2, dst + 2 * x2);
+    }
+}
+
+__device__ __forceinline__ bool aligned8(const void* p) { return ((unsigned long long)p & 7ull) == 0; }
+
+// two adjacent values of a storage array (8 / 4 / 4 bytes, aligned)
+template <typename T> __device__ __forceinline__ void store_pair(T* p, float a, float b);
+template <> __device__ __forceinline__ void store_pair<float>(float* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+template <> __device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+}
+template <> __device__ __forceinline__ void store_pair<__half>(__half* p, float a, float b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+}
+template <typename T> __device__ __forceinline__ float2 load_pair(const T* p);
+template <> __device__ __forceinline__ float2 load_pair<float>(const float* p) {
+    return *reinterpret_cast<const float2*>(p);
+}
+template <> __device__ __forceinline__ float2 load_pair<__nv_bfloat16>(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+template <> __device__ __forceinline__ float2 load_pair<__half>(const __half* p) {
+    return __half22float2(*reinterpret_cast<const __half2*>(p));
+}
+
 // ------------------------------------------------------------ reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
