@@ -78,6 +78,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Wait for the phase of `parity` to complete, for at most kWaitNs; with an
 // abort flag, also give up as soon as another warp of the CTA has raised it.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, const volatile int* abort = nullptr) {
+    if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -461,6 +462,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             int flush = 0;
             int vc = 0;
             int tin = ta - RT;
+            int so_next = ta % NS;                                   // stage of the next output frame
+            TS* zp = Z ? Z + (long long)ta * g.plane + (long long)yy * g.pitch + xg : nullptr;
             // One input frame tin; U = (tin - (ta - RT)) mod NR is the ring phase,
             // a compile-time constant, so the ring slots are fixed registers.
             auto frame = [&](auto phase) {
@@ -497,7 +500,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     // on the stage's mbarrier), and A's FULL arrival for o happened
                     // after that wait; this warp has since observed FULL of o and of
                     // the RT frames after it, so the load's bytes are visible here.
-                    const int so = o % NS;
+                    const int so = so_next;
+                    so_next = (so_next + 1 == NS) ? 0 : so_next + 1;
                     const unsigned char* st = stages + so * C::STAGE;
                     const int off = (brow + RY) * BOXW + XPAD + 4 * lane;
                     float xs[4], sps[4], fs[4], z[4];
@@ -540,7 +544,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 #pragma unroll
                                 for (int i = 0; i < 4; ++i) z[i] = to_f(from_f<TS>(z[i]));
                             }
-                            Vec4<TS>::store(Z + (long long)o * g.plane + (long long)yy * g.pitch + xg, z);
+                            Vec4<TS>::store(zp, z);
                         }
                     }
                     if (out_lane && !(MC && P.no_reduce)) {
@@ -553,6 +557,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                             part[3] = fmaf(dz, dz, part[3]);
                         }
                     }
+                    if (zp) zp += g.plane;
                     if (++flush == 16) {          // at most 64 FP32 terms per lane
                         flush = 0;
                         warp_flush(part, acc);
