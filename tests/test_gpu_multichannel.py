@@ -145,3 +145,25 @@ def test_channel_passes_match_any_radius_kernel(cuda_device, C, radii, sig):
     np.testing.assert_allclose(t1["rayleigh"], t2["rayleigh"], rtol=1e-6)
     assert rel_l2(y1, y2) < 1e-6
     assert abs(l1 - l2) < 1e-6 * abs(l2)
+
+
+def test_channel_passes_batched_match_single(cuda_device):
+    """The per-channel passes of the specialised kernel in a batched context
+    (per-video partial sums): each video equals its own single-video run and
+    the any-radius kernel's result."""
+    import torch
+    dims = [(5, 30, 120), (7, 26, 90), (4, 40, 112)]
+    radii, sig, K = (2, 4, 4), (1.5, 2.5, 2.5), 9
+    feats = [_features(d, 2, 700 + i) for i, d in enumerate(dims)]
+    res = {}
+    for flags in (0, sf.SFSEG_GENERIC):
+        eng = sf.SFSeg(batch_shapes=dims, radii=radii, sigmas=sig, alpha=1.0, p=0.1, nchan=2, flags=flags)
+        xs = [to_dev(s) for s, _ in feats]
+        eng.power_iterate_batched([to_dev(s) for s, _ in feats], [to_dev(f) for _, f in feats], xs, K)
+        torch.cuda.synchronize()
+        eng.close()
+        res[flags] = [x.cpu().numpy() for x in xs]
+    for i, ((s, f), d) in enumerate(zip(feats, dims)):
+        x1, _, _ = _gpu(d, s, f, s, K, radii, sig, 1.0, 0.1, nchan=2)
+        assert rel_l2(res[0][i], x1) < 1e-6
+        assert rel_l2(res[0][i], res[sf.SFSEG_GENERIC][i]) < 1e-6
