@@ -204,6 +204,53 @@ def workload_config(wl, storage, prob=None):
     return cfg
 
 
+def pipelined_calls(steps, stream, h2d, compute, d2h):
+    """`steps` end-to-end calls as a stream of inputs, two buffer slots: call
+    i's host->device copy h2d(i % 2) runs on its own stream and overlaps call
+    i-1's compute(), its device->host read d2h(i % 2) runs on a third stream
+    and overlaps call i+1's compute().  Every call's copies lie inside the
+    returned time (ms per call, CUDA events on `stream`)."""
+    import torch
+    s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    comp_done = [torch.cuda.Event() for _ in range(2)]
+    d2h_done = [torch.cuda.Event() for _ in range(2)]
+    started = [False, False]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def issue_h2d(i):
+        j = i & 1
+        with torch.cuda.stream(s_h2d):
+            if started[j]:
+                s_h2d.wait_event(comp_done[j])        # call i-2 no longer reads slot j
+            h2d(j)
+            h2d_done[j].record(s_h2d)
+
+    t0.record(stream)
+    s_h2d.wait_event(t0)
+    issue_h2d(0)
+    for i in range(steps):
+        j = i & 1
+        if i + 1 < steps:
+            issue_h2d(i + 1)
+        stream.wait_event(h2d_done[j])
+        if started[j]:
+            stream.wait_event(d2h_done[j])            # call i-2's result was read
+        compute(j)
+        comp_done[j].record(stream)
+        started[j] = True
+        with torch.cuda.stream(s_d2h):
+            s_d2h.wait_event(comp_done[j])
+            d2h(j)
+            d2h_done[j].record(s_d2h)
+    for j in range(2):
+        if started[j]:
+            stream.wait_event(d2h_done[j])
+    t1.record(stream)
+    t1.synchronize()
+    return t0.elapsed_time(t1) / steps
+
+
 class SingleVideo:
     """One seeded video of a named workload (FP32 / BF16 / FP16 storage); with
     several pairwise channels (Eq. 9) S is channel 0 and x0 = S."""
@@ -237,59 +284,26 @@ class SingleVideo:
         self.out_host.copy_(self.x, non_blocking=True)
 
     def e2e_pipeline(self, steps, stream):
-        """`steps` end-to-end calls as a stream of videos: call i's host->device
-        copy (its own stream, double-buffered) overlaps call i-1's compute, and
-        its device->host read (a third stream) overlaps call i+1's compute.
-        Every call's copies lie inside the returned time (ms, on `stream`)."""
         import torch
         if not hasattr(self, "_pipe"):
-            self._pipe = {
-                "fd": [torch.empty_like(self.f_dev) for _ in range(2)],
-                "x": [torch.empty_like(self.x) for _ in range(2)],
-                "oh": [torch.empty_like(self.out_host).pin_memory() for _ in range(2)],
-                "h2d": torch.cuda.Stream(), "d2h": torch.cuda.Stream()}
+            self._pipe = {"fd": [torch.empty_like(self.f_dev) for _ in range(2)],
+                          "x": [torch.empty_like(self.x) for _ in range(2)],
+                          "oh": [torch.empty_like(self.out_host).pin_memory() for _ in range(2)]}
         pp = self._pipe
-        ev = lambda: torch.cuda.Event()
-        h2d_done = [ev(), ev()]
-        comp_done = [ev(), ev()]
-        d2h_done = [ev(), ev()]
-        started = [False, False]
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-        def h2d(i):
-            j = i & 1
-            with torch.cuda.stream(pp["h2d"]):
-                if started[j]:
-                    pp["h2d"].wait_event(comp_done[j])      # call i-2 no longer reads it
-                pp["fd"][j].copy_(self.f_host, non_blocking=True)
-                h2d_done[j].record(pp["h2d"])
+        def h2d(j):
+            pp["fd"][j].copy_(self.f_host, non_blocking=True)
 
-        t0.record(stream)
-        pp["h2d"].wait_event(t0)
-        h2d(0)
-        for i in range(steps):
-            j = i & 1
-            if i + 1 < steps:
-                h2d(i + 1)
-            stream.wait_event(h2d_done[j])
-            if started[j]:
-                stream.wait_event(d2h_done[j])              # call i-2's result was read
+        def compute(j):
             fd, x = pp["fd"][j], pp["x"][j]
             s_dev = fd if self.wl.nchan == 1 else fd[0]
             x.copy_(s_dev)
             self.eng.power_iterate(s_dev, fd, x, self.K, out=x)
-            comp_done[j].record(stream)
-            started[j] = True
-            with torch.cuda.stream(pp["d2h"]):
-                pp["d2h"].wait_event(comp_done[j])
-                pp["oh"][j].copy_(x, non_blocking=True)
-                d2h_done[j].record(pp["d2h"])
-        for j in range(2):
-            if started[j]:
-                stream.wait_event(d2h_done[j])
-        t1.record(stream)
-        t1.synchronize()
-        return t0.elapsed_time(t1) / steps
+
+        def d2h(j):
+            pp["oh"][j].copy_(pp["x"][j], non_blocking=True)
+
+        return pipelined_calls(steps, stream, h2d, compute, d2h)
 
     def check(self):
         import torch
@@ -335,6 +349,29 @@ class Batch:
         self.eng.power_iterate_batched(self.f_dev, self.f_dev, self.xs, self.K)
         for oh, x in zip(self.out_host, self.xs):
             oh.copy_(x, non_blocking=True)
+
+    def e2e_pipeline(self, steps, stream):
+        import torch
+        if not hasattr(self, "_pipe"):
+            self._pipe = {"fd": [[torch.empty_like(t) for t in self.fs] for _ in range(2)],
+                          "x": [[torch.empty_like(t) for t in self.xs] for _ in range(2)],
+                          "oh": [[torch.empty_like(t).pin_memory() for t in self.out_host] for _ in range(2)]}
+        pp = self._pipe
+
+        def h2d(j):
+            for fd, fh in zip(pp["fd"][j], self.f_host):
+                fd.copy_(fh, non_blocking=True)
+
+        def compute(j):
+            for x, fd in zip(pp["x"][j], pp["fd"][j]):
+                x.copy_(fd)
+            self.eng.power_iterate_batched(pp["fd"][j], pp["fd"][j], pp["x"][j], self.K)
+
+        def d2h(j):
+            for oh, x in zip(pp["oh"][j], pp["x"][j]):
+                oh.copy_(x, non_blocking=True)
+
+        return pipelined_calls(steps, stream, h2d, compute, d2h)
 
     def check(self):
         import torch
