@@ -143,28 +143,41 @@ def rank_video_index(rank):
 
 def cpu_baseline(wl, seconds_hint: float = 15.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded
-    sample of the workload: the first `nf_s` frames of the same video and a
-    few power steps."""
+    sample of the workload, in the workload's unit (voxel-iterations / s):
+    the video (all its frames) and 4 power steps; for the batch its first
+    video; for the differentiable form 8 frames, 4 steps forward plus the
+    oracle's reverse mode (the bench step there is forward + adjoint)."""
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
-    import numpy as np
     import oracle
     from paper_1907_02731_gb300 import inputs
-    s, f = inputs.workload_features(wl.name)
-    nf_s, iters = wl.nf, 4
-    sub = np.ascontiguousarray(s[:nf_s], dtype=np.float64)
-    fsub = np.ascontiguousarray(f[..., :nf_s, :, :], dtype=np.float64)
     radii = (wl.rt, wl.ry, wl.rx)
     sig = (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
+    iters = 4
+    if wl.name.startswith("batch"):
+        nf, h, w = inputs.batch_layout()[0]
+        s = inputs.make_video(nf, h, w, inputs.config_seed(inputs.BATCH_CONFIG, 0), 2)[0]
+        f, what = s, f"the first video of the batch ({w}x{h}x{nf})"
+    else:
+        s, f = inputs.workload_features(wl.name)
+        what = f"the {wl.w}x{wl.h}x{wl.nf} video"
+    grad = wl.name.startswith("grad")
+    nf_s = 8 if grad else s.shape[0]
+    sub = np.ascontiguousarray(s[:nf_s], dtype=np.float64)
+    fsub = np.ascontiguousarray(f[..., :nf_s, :, :], dtype=np.float64)
     sp = oracle.unary(sub, wl.p)
     t0 = time.perf_counter()
-    oracle.power_iterate(sp, fsub, sub, iters, radii, sig, wl.alpha)
+    if grad:
+        target = (sub > 0.5).astype(np.float64)
+        oracle.adjoint(sp, fsub, sub, iters, radii, sig, wl.alpha, target)
+        what = f"the first {nf_s} frames of " + what + ", forward + reverse mode"
+    else:
+        oracle.power_iterate(sp, fsub, sub, iters, radii, sig, wl.alpha)
     dt = time.perf_counter() - t0
     vox_iter = sub.size * iters
     return {"value": vox_iter / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle",
-            "sample": f"first {nf_s} of {wl.nf} frames of the {wl.w}x{wl.h} video, {iters} FP64 "
-                      f"power steps, explicit edge-by-edge M ({dt:.1f} s)"}
+            "sample": f"{what}, {iters} FP64 power steps, explicit edge-by-edge M ({dt:.1f} s)"}
 
 
 def run_reference(args, wl):
