@@ -1,7 +1,7 @@
 // step_fast.cu -- the power step y = M x_hat (Eq. 7 x alpha) for the common
 // radii, specialised at compile time.
 //
-// Work decomposition.  A video is cut into 112 x 16 (x, y) tiles; one unit is
+// Work decomposition.  A video is cut into 112 x 12 (x, y) tiles; one unit is
 // one output frame of one tile.  Persistent CTAs (one of 512 threads per SM)
 // first stream one whole tile each, all in step (frame t of neighbouring
 // tiles is loaded at about the same time, so the halo rows one CTA loads are
@@ -10,27 +10,35 @@
 // [ta, tb)); a segment that starts or ends inside a video recomputes the
 // 2 RT boundary frames' spatial passes.
 //
-// Per segment the CTA streams frames.  For each input frame:
+// Per segment the CTA streams frames, with two warp roles that overlap:
 //   load    one thread issues three TMA 3D box loads (x, sp, f) of the tile
-//           plus its halo (128 x (16 + 2 RY)) into a ring of RT + 2 shared-
-//           memory stages (zero fill outside the volume = the zero padding of
-//           Eq. 7's convolutions), one frame ahead, completion on an mbarrier;
-//   y-pass  warps 0..7: a task is a column pair x 4 output rows; a0 = sp x,
-//           a1 = f a0, a2 = f a1 and the vertical taps in registers, every
-//           channel packed over the column pair (FMUL2 / FFMA2);
-//   x-pass  warp w owns output row w; lanes 0..27 own 4 output columns each,
-//           lanes 28..31 hold the 2 x 4 halo columns, so every halo value
-//           comes from one shuffle with a source lane fixed per thread;
+//           plus its halo (128 x (12 + 2 RY)) into a ring of RT + 2 + LA
+//           shared-memory stages (zero fill outside the volume = the zero
+//           padding of Eq. 7's convolutions), LA frames ahead, completion on
+//           an mbarrier per stage;
+//   y-pass  warps 0..3 ("A"): a task is a column pair x 6 output rows;
+//           a0 = sp x, a1 = f a0, a2 = f a1 and the vertical taps in
+//           registers, every channel packed over the column pair (FMUL2 /
+//           FFMA2); (a0, a1) are stored interleaved per column in a swizzled
+//           plane, a2 in its own plane, double-buffered; FULL mbarrier;
+//   x-pass  warps 4..15 ("B"): warp w owns output row w - 4, lanes 0..27 four
+//           output columns each, windows read straight from shared memory;
+//           (a0, a1) filtered with packed FMAs, a2 with scalar ones;
 //   t-pass  each thread keeps 2 RT + 1 partial sums per voxel and channel in
-//           registers; the slot roles are static per ring phase (a switch on
-//           the phase selects one of 2 RT + 1 specialisations);
+//           registers; the frame loop is unrolled over the ring phase so the
+//           slot roles are fixed registers;
 //   combine y = sp [(1 - a f^2) C0 + 2 a f C1 - a C2] for frame t - RT, with
-//           the deferred scale and gain folded into the temporal taps;
-//           16-byte stores, FP32 partial sums of z.z, x.z, x.x, |z - s x|^2
-//           per thread, FP64 per warp and per segment.
-// The last CTA of each video to finish reduces the per-segment partials and
-// updates the video's scalars (no CTA waits on another).  Every mbarrier wait
-// is bounded; on timeout the CTA records SFSEG_ETIMEOUT and stops.
+//           the deferred scale and gain; 16-byte stores; FP32 partial sums of
+//           z.z, x.z, x.x, |z - s x|^2 per thread over at most 16 frames, FP64
+//           per warp; EMPTY mbarrier back to the y-pass warps.
+// Consecutive segments of one video on a CTA form a run with one FP64
+// reduction and one arrival; the last CTA of each video to arrive reduces the
+// partials and updates the video's scalars (no CTA waits on another).
+// Variants (template flags): AUX also stores the per-voxel terms the adjoint
+// needs; MC runs several pairwise channels (Eq. 9) as one pass per channel,
+// each adding to the partial sum in the output buffer.  Every device wait is
+// limited in time and gives up when another warp of the CTA has; a CTA that
+// gives up drains its loads, records SFSEG_ETIMEOUT and leaves.
 #include <cuda.h>
 
 #include <type_traits>
