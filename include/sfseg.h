@@ -166,6 +166,18 @@ sfseg_status sfseg_power_iterate_binarized(sfseg_ctx* ctx, const float* d_s, con
                                            float* d_x, int32_t n_iters, const sfseg_binarize* b,
                                            uint8_t* d_mask, void* stream);
 
+/* Warnings about the loaded features (bits of *flags):
+ *   SFSEG_WARN_NEGATIVE_M: alpha * (max f - min f)^2 > 1 for some video and
+ *     channel, so the Taylor affinity 1 - alpha (f_i - f_j)^2 of Eq. 2 can be
+ *     negative: M may have negative entries and the Perron-Frobenius argument
+ *     of Sec. 3 (a non-negative principal eigenvector) no longer holds.  The
+ *     computation itself is unaffected.
+ * The range is that of the stored f (after the storage rounding), tracked by
+ * the feature load.  Synchronises the device.  No features
+ * loaded: *flags = 0.  Errors: EINVAL, ECUDA. */
+#define SFSEG_WARN_NEGATIVE_M 1
+sfseg_status sfseg_get_warnings(sfseg_ctx* ctx, int32_t* flags);
+
 /* Test aid for failure detection (no counterpart in the paper).  The next
  * n_steps step launches of this context (specialised step kernel only) make
  * the first x-pass warp of every CTA wait on a barrier that nothing arrives

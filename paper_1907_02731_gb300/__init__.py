@@ -33,7 +33,9 @@ EXPORTS = (
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
     "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
     "sfseg_default_binarize", "sfseg_power_iterate_binarized", "sfseg_debug_inject_timeout",
+    "sfseg_get_warnings",
 )
+SFSEG_WARN_NEGATIVE_M = 1
 
 
 class sfseg_binarize(ctypes.Structure):
@@ -97,6 +99,7 @@ def load_library(path: str = LIB_PATH):
                                        _i32, ctypes.POINTER(_i32), _i32]),
         "sfseg_default_binarize": (None, [ctypes.POINTER(sfseg_binarize)]),
         "sfseg_debug_inject_timeout": (_i32, [_vp, _i32]),
+        "sfseg_get_warnings": (_i32, [_vp, ctypes.POINTER(_i32)]),
         "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
                                                  ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
@@ -339,6 +342,12 @@ class SFSeg:
         sfseg_power_iterate_binarized(self.ctx, ds, df, _dev_f32(x, "x").data_ptr(), iters, b,
                                       mask.data_ptr(), _stream_handle())
         return x, mask
+
+    def warnings(self) -> int:
+        """Bits of SFSEG_WARN_* about the loaded features (synchronises)."""
+        fl = _i32(0)
+        _check(load_library().sfseg_get_warnings(self.ctx, ctypes.byref(fl)), self.ctx)
+        return int(fl.value)
 
     def debug_inject_timeout(self, n_steps: int = 1):
         """Test aid: the next n_steps steps give up on a device-side wait and

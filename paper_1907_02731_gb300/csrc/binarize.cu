@@ -21,14 +21,6 @@
 
 namespace sfseg {
 
-__device__ __forceinline__ unsigned float_key(float v) {
-    const unsigned b = __float_as_uint(v);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float key_float(unsigned k) {
-    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
-
 __device__ __forceinline__ float block_max(float v) {
     __shared__ float sh[32];
 #pragma unroll

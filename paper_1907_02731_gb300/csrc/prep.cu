@@ -17,6 +17,20 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
     TS* SPo = (TS*)P.sp_out + g.off;
     TS* Fo = (TS*)P.f_out + g.off;
     int bad = 0;
+    float fmin[kMaxChan], fmax[kMaxChan];   // range of the stored f per channel
+#pragma unroll
+    for (int c = 0; c < kMaxChan; ++c) {
+        fmin[c] = INFINITY;
+        fmax[c] = -INFINITY;
+    }
+    auto track = [&](int c, float v) {
+#pragma unroll
+        for (int k = 0; k < kMaxChan; ++k)
+            if (k == c) {
+                fmin[k] = fminf(fmin[k], v);
+                fmax[k] = fmaxf(fmax[k], v);
+            }
+    };
     const bool pairs = aligned8(P.s) && aligned8(P.f) && (n % 2 == 0);
     for_each_voxel_pair(
         g, pairs,
@@ -30,6 +44,8 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
                 const float2 fv = *reinterpret_cast<const float2*>(P.f + c * n + i);
                 bad |= !isfinite(fv.x) | !isfinite(fv.y);
                 store_pair<TS>(Fo + c * P.chan_stride + o, fv.x, fv.y);
+                track(c, to_f(from_f<TS>(fv.x)));
+                track(c, to_f(from_f<TS>(fv.y)));
             }
         },
         [&](long long i, long long o) {
@@ -41,9 +57,37 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
                 const float fv = P.f[c * n + i];
                 bad |= !isfinite(fv);
                 Fo[c * P.chan_stride + o] = from_f<TS>(fv);
+                track(c, to_f(from_f<TS>(fv)));
             }
         });
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.bad, 1);
+    // range of f per channel: warp, then block, then one atomic per block
+    __shared__ float s_min[kMaxChan][8], s_max[kMaxChan][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < kMaxChan; ++c) {
+        float lo = fmin[c], hi = fmax[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+        }
+        if (lane == 0) {
+            s_min[c][warp] = lo;
+            s_max[c][warp] = hi;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < P.nchan && P.fmin_key) {
+        const int c = threadIdx.x;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fminf(lo, s_min[c][w]);
+            hi = fmaxf(hi, s_max[c][w]);
+        }
+        atomicMin(&P.fmin_key[c], float_key(lo));
+        atomicMax(&P.fmax_key[c], float_key(hi));
+    }
 }
 
 template <typename TS>

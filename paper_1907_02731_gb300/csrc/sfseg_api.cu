@@ -73,6 +73,9 @@ struct sfseg_ctx {
     unsigned char* d_adj_misc = nullptr;
     // test aid: step launches still to run with an injected device-side timeout
     int inject_steps = 0;
+    // range of the loaded f per video and channel: float keys [nv][kMaxChan]
+    unsigned* d_fmin = nullptr;
+    unsigned* d_fmax = nullptr;
     void* d_adj = nullptr;      // [C + 4] volumes: recompute ring, g ping-pong, dsp, df
     int adj_cap = 0;
     double* d_adjc = nullptr;   // [2] dot products
@@ -152,7 +155,7 @@ static void free_ctx(sfseg_ctx* c) {
                     c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps,
                     c->d_gitems, c->d_gitem_begin, c->d_gpartials, c->d_rec, c->d_rrec,
                     c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter, c->d_bin,
-                    c->d_adj_misc};
+                    c->d_adj_misc, c->d_fmin, c->d_fmax};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -407,6 +410,8 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
     ALLOC(c->d_prep_counter, sizeof(unsigned));
     ALLOC(c->d_bad, sizeof(int));
     ALLOC(c->d_out, sizeof(float*) * nv);
+    ALLOC(c->d_fmin, sizeof(unsigned) * kMaxChan * nv);
+    ALLOC(c->d_fmax, sizeof(unsigned) * kMaxChan * nv);
     ALLOC(c->d_gitems, sizeof(WorkItem) * gitems.size());
     ALLOC(c->d_gitem_begin, sizeof(int) * gitem_begin.size());
     ALLOC(c->d_gpartials, sizeof(double) * kRed * gitems.size());
@@ -616,6 +621,10 @@ static sfseg_status load_features_impl(sfseg_ctx* c, const float* const* d_s, co
         P.p = (float)c->prm.p;
         P.s_is_sp = (c->prm.flags & SFSEG_S_IS_SP) ? 1 : 0;
         P.bad = c->d_bad;
+        P.fmin_key = c->d_fmin + kMaxChan * v;
+        P.fmax_key = c->d_fmax + kMaxChan * v;
+        CUDA_OR(c, cudaMemsetAsync(P.fmin_key, 0xff, sizeof(unsigned) * kMaxChan, s));
+        CUDA_OR(c, cudaMemsetAsync(P.fmax_key, 0, sizeof(unsigned) * kMaxChan, s));
         CUDA_OR(c, launch_prep_features(c->prm.storage, P, s));
         c->launches += 1;
     }
@@ -1220,6 +1229,30 @@ sfseg_status sfseg_adjoint(sfseg_ctx* c, const float* d_gx, float* d_gsp, float*
     if (d_gf) CUDA_OR(c, launch_pitch_copy(df, d_gf, g, 0, nullptr, s));
     c->launches += 3;
     c->last_stream = s;
+    return SFSEG_OK;
+}
+
+// key of a float as kept on the device (float_key), decoded on the host
+static float key_to_float(unsigned k) {
+    const unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float v;
+    memcpy(&v, &b, sizeof v);
+    return v;
+}
+
+sfseg_status sfseg_get_warnings(sfseg_ctx* c, int32_t* flags) {
+    if (!c || !flags) return fail(c, SFSEG_EINVAL, "ctx and flags must be non-NULL");
+    *flags = 0;
+    if (!c->features) return SFSEG_OK;
+    CUDA_OR(c, cudaDeviceSynchronize());   // the load may have run on any stream
+    std::vector<unsigned> lo((size_t)kMaxChan * c->nv), hi((size_t)kMaxChan * c->nv);
+    CUDA_OR(c, cudaMemcpy(lo.data(), c->d_fmin, sizeof(unsigned) * lo.size(), cudaMemcpyDeviceToHost));
+    CUDA_OR(c, cudaMemcpy(hi.data(), c->d_fmax, sizeof(unsigned) * hi.size(), cudaMemcpyDeviceToHost));
+    for (int v = 0; v < c->nv; ++v)
+        for (int ch = 0; ch < c->prm.nchan; ++ch) {
+            const double r = (double)key_to_float(hi[kMaxChan * v + ch]) - key_to_float(lo[kMaxChan * v + ch]);
+            if (c->prm.alpha * r * r > 1.0) *flags |= SFSEG_WARN_NEGATIVE_M;
+        }
     return SFSEG_OK;
 }
 

@@ -182,6 +182,17 @@ template <> __device__ __forceinline__ float2 load_pair<__half>(const __half* p)
     return __half22float2(*reinterpret_cast<const __half2*>(p));
 }
 
+// Order-preserving map of float bits onto unsigned integers: atomicMax /
+// atomicMin on the keys are max / min on the floats (key 0 is below every
+// float, 0xffffffff above).
+__device__ __forceinline__ unsigned float_key(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 // ------------------------------------------------------------ reductions
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

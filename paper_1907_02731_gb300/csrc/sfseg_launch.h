@@ -21,6 +21,8 @@ struct PrepFeatParams {
     float p;
     int s_is_sp;
     int* bad;                   // set to 1 if a non-finite input is seen
+    unsigned* fmin_key;         // [nchan] float_key of the minimum of the stored f (all ones before)
+    unsigned* fmax_key;         // [nchan] float_key of the maximum (zero before); both may be null
 };
 
 struct PrepXParams {

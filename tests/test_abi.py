@@ -88,3 +88,8 @@ def test_noalloc_rejects_channels(lib):
 
 def test_debug_injection_null_context(lib):
     assert lib.sfseg_debug_inject_timeout(None, 1) == sf.SFSEG_EINVAL
+
+
+def test_warnings_null_arguments(lib):
+    flags = ctypes.c_int32(7)
+    assert lib.sfseg_get_warnings(None, ctypes.byref(flags)) == sf.SFSEG_EINVAL

@@ -123,3 +123,25 @@ def test_binarized_and_adjoint_writes_stay_inside(cuda_device):
         assert all(torch.isfinite(t).all() for t in (gsp, gf, gx0))
     finally:
         eng.close()
+
+
+@pytest.mark.parametrize("alpha,scale2,expect", [(1.0, 1.0, 0), (1.5, 1.0, 1), (1.0, 2.0, 1)])
+def test_negative_affinity_warning(cuda_device, alpha, scale2, expect):
+    """alpha * (max f - min f)^2 > 1 on some channel: the Taylor affinity can
+    be negative and Perron-Frobenius no longer applies; the feature load
+    reports it (the features here span [0, 1] before scaling)."""
+    f = _video()
+    f = (f - f.min()) / (f.max() - f.min())          # range exactly 1
+    two = torch_stack([f, f * scale2])
+    eng = sf.SFSeg(SHAPE, radii=RADII, sigmas=SIG, alpha=alpha, nchan=2)
+    try:
+        assert eng.warnings() == 0                   # nothing loaded yet
+        eng.load_features(f, two)
+        assert eng.warnings() == expect * sf.SFSEG_WARN_NEGATIVE_M
+    finally:
+        eng.close()
+
+
+def torch_stack(ts):
+    import torch
+    return torch.stack(ts).contiguous()
