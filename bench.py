@@ -540,6 +540,9 @@ def run_ours(args, wl):
                          "frac": achieved / peak,
                          "traffic": DRAM_TRAFFIC_PER_LAUNCH.get((wl.name, args.storage)),
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
+                         "frac_physical": (DRAM_TRAFFIC_PER_LAUNCH[(wl.name, args.storage)]
+                                           / (step_ms / 1e3) / 1e9 / peak
+                                           if (wl.name, args.storage) in DRAM_TRAFFIC_PER_LAUNCH else None),
                          "algorithmic_bytes_per_launch": bpv * prob.n,
                          "peak_kind": peak_kind,
                          "kernel": "power step (fused stencil%s)" % (
