@@ -518,7 +518,7 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
     for (int d = 0; d < 2 * kMaxRt + 1; ++d) P.gt2[d] = make_float2(P.gt[d], P.gt[d]);
     for (int d = 0; d < 2 * kMaxR + 1; ++d) {
         P.gy2[d] = make_float2(P.gy[d], P.gy[d]);
-        P.gx2[d] = make_float2(P.gx[d], P.gx[d]);
+        P.gx2[d] = make_float2(P.gx[d], -2.f * P.gx[d]);   // channel b carries -2 (exact)
     }
     P.maps = c->d_maps;
     P.x_sel = k & 1;

@@ -84,7 +84,7 @@ struct StepParams {
     // specialised kernel only
     float2 gt2[2 * kMaxRt + 1];  // each tap twice, the paired operand of the packed FMAs
     float2 gy2[2 * kMaxR + 1];
-    float2 gx2[2 * kMaxR + 1];
+    float2 gx2[2 * kMaxR + 1];  // (g, -2 g): the x-pass of the (a, b) pair yields (C0, -2 C1), exactly
     const void* maps;           // [n_videos][4] CUtensorMap: sp, f, x_a, x_b (global memory)
     int x_sel;                  // 0: the input iterate is x_a, 1: x_b
     const int* cta_begin;       // [n_ctas + 1]: segments of CTA c are [cta_begin[c], cta_begin[c+1])

@@ -23,7 +23,8 @@
 //           plane, a2 in its own plane, double-buffered; FULL mbarrier;
 //   x-pass  warps 4..15 ("B"): warp w owns output row w - 4, lanes 0..27 four
 //           output columns each, windows read straight from shared memory;
-//           (a0, a1) filtered with packed FMAs, a2 with scalar ones;
+//           (a0, a1) filtered with packed FMAs (a1's taps carry the factor
+//           -2 of the combine, exact in binary), a2 with scalar ones;
 //   t-pass  each thread keeps 2 RT + 1 partial sums per voxel and channel in
 //           registers; the frame loop is unrolled over the ring phase so the
 //           slot roles are fixed registers;
@@ -520,13 +521,13 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         // scale and gain applied here; t1 = f C0 - 2 C1
-                        const float t1 = fmaf(fs[i], cab[i].x, -2.f * cab[i].y);
+                        const float t1 = fmaf(fs[i], cab[i].x, cab[i].y);   // cab[i].y = -2 C1
                         const float t2 = fmaf(fs[i], t1, c2[i]);
                         const float kb = fmaf(-alpha, t2, cab[i].x);
                         z[i] = (sg_s * sps[i]) * kb;
                         if (AUX) {
                             ak[i] = kb;
-                            af[i] = t1 + cab[i].y;
+                            af[i] = fmaf(-0.5f, cab[i].y, t1);   // f C0 - C1
                         }
                     }
                     if (MC && P.acc_in && st_ok && xg < g.pitch) {   // earlier channels' passes (Eq. 9 sums them)
