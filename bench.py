@@ -603,14 +603,118 @@ def run_accuracy(args):
 SWEEP_SHAPES = ((10, 20, 20), (10, 60, 107), (20, 120, 214), (36, 240, 427), (72, 480, 854))
 
 
+# Largest graphs whose explicit Eq. 2 matrix the sweep builds: on the GPU
+# (cuSPARSE through torch; ~300 M stored entries at 513,600 nodes) and on the
+# host (scipy; ~39 M entries at 64,200 nodes).  The full video's matrix would
+# hold ~1.8e10 entries.
+SPARSE_GPU_MAX_NODES = 600_000
+SPARSE_CPU_MAX_NODES = 100_000
+
+
+def explicit_eq2_matrix(sp, f, radii, sigmas, alpha):
+    """The N x N matrix of Eq. 2 built explicitly (the comparison of Fig. 2:
+    power iteration on a stored sparse adjacency): one diagonal band per
+    offset (dt, dy, dx) of the Gaussian box, M_ij = sp_i sp_j (1 - alpha
+    (f_i - f_j)^2) g_t g_y g_x, zero outside the volume.  sp, f: FP32 torch
+    tensors [nf, h, w] on the device that builds it; returns torch CSR."""
+    import torch
+    nf, h, w = sp.shape
+    dev = sp.device
+    idx = torch.arange(nf * h * w, device=dev, dtype=torch.int64).reshape(nf, h, w)
+    taps = [[math.exp(-d * d / (2.0 * s * s)) for d in range(-r, r + 1)] for r, s in zip(radii, sigmas)]
+
+    def cut(d, n):   # (source, neighbour) index ranges along one axis for offset d
+        return slice(max(0, -d), n - max(0, d)), slice(max(0, d), n - max(0, -d))
+    rows, cols, vals = [], [], []
+    rt, ry, rx = radii
+    for dt in range(-rt, rt + 1):
+        ti, tj = cut(dt, nf)
+        for dy in range(-ry, ry + 1):
+            yi, yj = cut(dy, h)
+            for dx in range(-rx, rx + 1):
+                xi, xj = cut(dx, w)
+                if ti.start >= ti.stop or yi.start >= yi.stop or xi.start >= xi.stop:
+                    continue
+                d = f[ti, yi, xi] - f[tj, yj, xj]
+                g = taps[0][dt + rt] * taps[1][dy + ry] * taps[2][dx + rx]
+                vals.append((sp[ti, yi, xi] * sp[tj, yj, xj] * (1.0 - alpha * d * d) * g).reshape(-1))
+                rows.append(idx[ti, yi, xi].reshape(-1))
+                cols.append(idx[tj, yj, xj].reshape(-1))
+    n = nf * h * w
+    ij = torch.stack([torch.cat(rows), torch.cat(cols)])
+    del rows, cols
+    A = torch.sparse_coo_tensor(ij, torch.cat(vals), (n, n), check_invariants=False).coalesce().to_sparse_csr()
+    return A
+
+
+def sparse_baselines(f, sp, wl, iters, x_ours):
+    """Fig. 2's comparison at one size: build the explicit matrix and run
+    `iters` power steps on it (GPU: torch CSR / cuSPARSE; host: scipy), and
+    the host Lanczos (scipy eigsh) for the leading eigenvector.  Times in
+    seconds; x^iters of the GPU sparse run is checked against ours."""
+    import torch
+    radii, sig = (wl.rt, wl.ry, wl.rx), (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
+    n = f.numel()
+    out = {"sparse_gpu": None, "sparse_cpu": None, "lanczos_cpu": None}
+    if n <= SPARSE_GPU_MAX_NODES:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A = explicit_eq2_matrix(sp, f, radii, sig, wl.alpha)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        x = f.reshape(-1) / f.norm()
+        for _ in range(3):   # warm-up of the SpMV path
+            y = A @ x
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        for _ in range(iters):
+            y = A @ x
+            x = y / y.norm()
+        e[1].record()
+        torch.cuda.synchronize()
+        err = float((x - x_ours.reshape(-1)).norm() / x_ours.norm())
+        out["sparse_gpu"] = {"build_s": t_build, "iters_s": e[0].elapsed_time(e[1]) / 1e3,
+                             "nnz": int(A.values().numel()), "rel_l2_vs_ours": err}
+        del A, x, y
+        torch.cuda.empty_cache()
+    if n <= SPARSE_CPU_MAX_NODES:
+        import scipy.sparse as ssp
+        import scipy.sparse.linalg as sla
+        fc, spc = f.cpu(), sp.cpu()
+        t0 = time.perf_counter()
+        Ac = explicit_eq2_matrix(spc, fc, radii, sig, wl.alpha)
+        A = ssp.csr_matrix((Ac.values().numpy(), Ac.col_indices().numpy(), Ac.crow_indices().numpy()),
+                           shape=(n, n))
+        t_build = time.perf_counter() - t0
+        x = fc.reshape(-1).numpy().astype(np.float32)
+        x /= np.linalg.norm(x)
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            y = A @ x
+            x = y / np.linalg.norm(y)
+        t_it = time.perf_counter() - t0
+        out["sparse_cpu"] = {"build_s": t_build, "iters_s": t_it, "threads": 1}
+        t0 = time.perf_counter()
+        sla.eigsh(A.astype(np.float64), k=1, which="LA", tol=1e-8)
+        out["lanczos_cpu"] = {"eigsh_s": time.perf_counter() - t0}
+    return out
+
+
 def run_sweep(args):
     """Runtime of one power step against the number of nodes (Fig. 2): the
     same 11x11x5 kernel and seeded video recipe from the paper's 4000-node toy
-    to the full 854x480x72 video; one JSON line per size."""
+    to the full 854x480x72 video; one JSON line per size.  With --sweep-sparse
+    the line adds Fig. 2's comparison: 100 power steps on the explicitly built
+    sparse matrix (GPU and host) and host Lanczos, up to the sizes whose
+    matrix is practical to store."""
     import torch
     import paper_1907_02731_gb300 as sf
     from paper_1907_02731_gb300 import inputs
     wl = inputs.WORKLOADS["video_72x480x854"]
+    if args.sweep_sparse:   # torch's sparse set-up and cuSPARSE handles, outside the timings
+        t = torch.rand(2, 4, 4, device="cuda")
+        _ = explicit_eq2_matrix(t, t, (1, 1, 1), (1.0, 1.0, 1.0), 1.0) @ t.reshape(-1)
+        torch.cuda.synchronize()
     for shape in SWEEP_SHAPES:
         f_np, _ = inputs.make_video(*shape, inputs.config_seed(wl.config, 0), wl.n_distractors)
         f = torch.from_numpy(f_np).cuda()
@@ -636,10 +740,24 @@ def run_sweep(args):
         torch.cuda.synchronize()
         step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / wl.iters
         n = int(np.prod(shape))
-        print(json.dumps({"sweep": "power step vs nodes", "shape": list(shape), "nodes": n,
-                          "storage": args.storage, "flags": args.sweep_flags, "us_per_step": step_ms * 1e3,
-                          "voxel_iter_per_s": n / (step_ms / 1e3),
-                          "call_ms_50_steps": e[0].elapsed_time(e[1]) / reps}))
+        line = {"sweep": "power step vs nodes", "shape": list(shape), "nodes": n,
+                "storage": args.storage, "flags": args.sweep_flags, "us_per_step": step_ms * 1e3,
+                "voxel_iter_per_s": n / (step_ms / 1e3),
+                "call_ms_50_steps": e[0].elapsed_time(e[1]) / reps}
+        if args.sweep_sparse:
+            # Fig. 2 counts 100 iterations including the set-up: one call of
+            # 100 steps (feature preparation included) against the explicit
+            # matrix's build plus 100 sparse power steps
+            x.copy_(f)
+            torch.cuda.synchronize()
+            e[0].record()
+            eng.power_iterate(f, f, x, 100, out=x)
+            e[1].record()
+            torch.cuda.synchronize()
+            line["ours_100_iters_s"] = e[0].elapsed_time(e[1]) / 1e3
+            sp = f.clamp_min(0) ** wl.p if wl.p != 1.0 else f
+            line.update(sparse_baselines(f, sp, wl, 100, x))
+        print(json.dumps(line), flush=True)
         eng.close()
 
 
@@ -656,6 +774,8 @@ def main():
                     help="report x^K errors of FP32/BF16/FP16 storage against the FP64 oracle")
     ap.add_argument("--sweep", action="store_true",
                     help="time one power step at sizes from 4000 nodes to the full video")
+    ap.add_argument("--sweep-sparse", action="store_true",
+                    help="with --sweep: also time the explicit sparse matrix (GPU, host) and host Lanczos")
     ap.add_argument("--sweep-flags", type=int, default=0,
                     help="context flags for --sweep (8: any-radius kernel, 16: autotune)")
     args = ap.parse_args()
