@@ -42,6 +42,27 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 DRAM_TRAFFIC_PER_LAUNCH = {("video_72x480x854", "f32"): 367.878144e6 + 99.450112e6}
 
 
+def alu_flops_per_voxel(wl) -> int:
+    """Algorithmic FP32 flops of one voxel-iteration (an FMA counts 2), no
+    halo recompute: pre-products a = sp x, b_c = f_c a, c = sum f_c^2 a
+    (1 + 2C); the separable taps of the 2 + C convolutions (Eq. 9; 3 for one
+    channel); the combine (8 per channel); the four per-voxel reduction
+    terms z.z, x.z, x.x and |z - r x|^2 (10)."""
+    C = wl.nchan
+    nconv = 3 if C == 1 else C + 2
+    taps = (2 * wl.rt + 1) + (2 * wl.ry + 1) + (2 * wl.rx + 1)
+    return (1 + 2 * C) + nconv * taps * 2 + 8 * C + 10
+
+
+def alu_peak_tflops(sm_max_mhz=None) -> float:
+    """Plain FP32 pipe peak of this GPU: SMs x 128 FP32 lanes x 2 flops x the
+    maximum SM clock (nvidia-smi's clocks.max.sm, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(sm_max_mhz) if sm_max_mhz else 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -557,6 +578,22 @@ def run_ours(args, wl):
             "gpu_launches": int(launches),
             "check": check,
         }
+        # the ALU roofline: the FP32 stencil sits near the ridge; with 2-byte
+        # storage the step is bound by its FP32 arithmetic, not its bytes
+        clk_sum = line["clocks"] if isinstance(line["clocks"], dict) else {}
+        fpv = alu_flops_per_voxel(wl)
+        alu_peak = alu_peak_tflops(clk_sum.get("sm_max_mhz"))
+        alu_ach = fpv * prob.n / (step_ms / 1e3) / 1e12
+        alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": alu_ach / alu_peak, "traffic": None, "flops_per_voxel": fpv,
+               "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+               "step_us": step_ms * 1e3}
+        if args.storage == "f32":
+            line["roofline_alu"] = alu
+        else:
+            line["roofline_hbm"] = line["roofline"]
+            alu["traffic"] = line["roofline_hbm"]["traffic"]
+            line["roofline"] = alu
         if args.cpu_baseline and world == 1 and kind is SingleVideo:
             line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line))
