@@ -133,10 +133,10 @@ __global__ void __launch_bounds__(AJ_THREADS) adjoint_kernel(const __grid_consta
         s_last = (prev + 1u == gridDim.x);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    double tot = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(&P.partials[b]);
+    const double tot = block_sum_partials(P.partials, (int)gridDim.x);
+    if (threadIdx.x != 0) return;
     *P.c_out = tot;
     *P.counter = 0u;
 }
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(256) dot_kernel(const float* x, const double* 
         s_last = (prev + 1u == gridDim.x);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    double tot = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(&partials[b]);
+    const double tot = block_sum_partials(partials, (int)gridDim.x);
+    if (threadIdx.x != 0) return;
     *out = tot * *scale_x;
     *counter = 0u;
 }
@@ -251,10 +251,10 @@ __global__ void __launch_bounds__(256) adj_combine_kernel(const __grid_constant_
         s_last = (atomicAdd(P.counter, 1u) + 1u == gridDim.x);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        double tot = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) tot += __ldcg(&P.partials[b]);
+    if (!s_last) return;
+    __threadfence();
+    const double tot = block_sum_partials(P.partials, (int)gridDim.x);
+    if (threadIdx.x == 0) {
         *P.c_out = tot;
         *P.counter = 0u;
     }

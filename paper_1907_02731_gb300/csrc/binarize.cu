@@ -12,7 +12,7 @@
 // Kernels:
 //   vmax_stored_kernel  max of the stored iterate of one video (pitched, storage type)
 //   project_kernel      p of every voxel, stored in place; FP64 block partials of p^2
-//   project_finish      fixed-order sum of the partials -> the video's scale 1 / ||p||
+//   project_finish      fixed-order sum of the partials (one block) -> the video's scale 1 / ||p||
 //   vmax_f32_kernel     max of a contiguous FP32 array (the caller's x)
 //   threshold_kernel    m = [x >= theta * max(x)] as bytes
 // Maxima go through an order-preserving map of the float bits onto unsigned
@@ -75,13 +75,12 @@ __global__ void __launch_bounds__(256) project_kernel(const __grid_constant__ Pr
 }
 
 __global__ void project_finish_kernel(const __grid_constant__ ProjectParams P) {
+    const double s = block_sum_partials(P.partials, P.n_blocks);
     if (threadIdx.x != 0) return;
     VState* st = P.state + P.video;
     const float vmax = key_float(*P.vmax_key);
     *P.vmax_key = 0u;   // ready for the next projection
     if (st->done) return;
-    double s = 0.0;
-    for (int b = 0; b < P.n_blocks; ++b) s += P.partials[b];
     if (!(vmax > 0.f) || !isfinite(vmax) || !(s > 0.0) || !isfinite(s)) {
         st->status = isfinite(vmax) && isfinite(s) ? 4 : 5;   // SFSEG_EZERONORM / SFSEG_ENONFINITE
         st->done = 1;
@@ -112,7 +111,7 @@ template <typename TS>
 static cudaError_t launch_project_t(const ProjectParams& P, cudaStream_t s) {
     vmax_stored_kernel<TS><<<P.n_blocks, 256, 0, s>>>(P);
     project_kernel<TS><<<P.n_blocks, 256, 0, s>>>(P);
-    project_finish_kernel<<<1, 32, 0, s>>>(P);
+    project_finish_kernel<<<1, 256, 0, s>>>(P);
     return cudaPeekAtLastError();
 }
 

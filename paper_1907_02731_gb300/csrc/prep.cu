@@ -31,35 +31,57 @@ __global__ void __launch_bounds__(256) prep_features_kernel(const __grid_constan
                 fmax[k] = fmaxf(fmax[k], v);
             }
     };
-    const bool pairs = aligned8(P.s) && aligned8(P.f) && (n % 2 == 0);
-    for_each_voxel_pair(
-        g, pairs,
-        [&](long long i, long long o) {
-            const float2 s = *reinterpret_cast<const float2*>(P.s + i);
-            const float sp0 = P.s_is_sp ? s.x : powf(s.x, P.p);
-            const float sp1 = P.s_is_sp ? s.y : powf(s.y, P.p);
-            bad |= !isfinite(s.x) | !isfinite(s.y) | !isfinite(sp0) | !isfinite(sp1);
-            store_pair<TS>(SPo + o, sp0, sp1);
-            for (int c = 0; c < P.nchan; ++c) {
-                const float2 fv = *reinterpret_cast<const float2*>(P.f + c * n + i);
-                bad |= !isfinite(fv.x) | !isfinite(fv.y);
-                store_pair<TS>(Fo + c * P.chan_stride + o, fv.x, fv.y);
-                track(c, to_f(from_f<TS>(fv.x)));
-                track(c, to_f(from_f<TS>(fv.y)));
+    auto one = [&](long long i, long long o) {
+        const float s = P.s[i];
+        const float sp = P.s_is_sp ? s : powf(s, P.p);
+        bad |= !isfinite(s) | !isfinite(sp);
+        SPo[o] = from_f<TS>(sp);
+        for (int c = 0; c < P.nchan; ++c) {
+            const float fv = P.f[c * n + i];
+            bad |= !isfinite(fv);
+            Fo[c * P.chan_stride + o] = from_f<TS>(fv);
+            track(c, to_f(from_f<TS>(fv)));
+        }
+    };
+    if (aligned8(P.s) && aligned8(P.f) && pair_batch_ok(g)) {
+        constexpr int U = 4;
+        for_each_pair_batch<U>(g, [&](const long long (&i)[U], const long long (&o)[U], const bool (&ok)[U]) {
+            float2 s[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) s[u] = *reinterpret_cast<const float2*>(P.s + i[u]);
+            // with S = F (one array) the F loads below hit the lines just read;
+            // the channel loop is unrolled so that each channel's range lives
+            // in registers
+#pragma unroll
+            for (int c = 0; c < kMaxChan; ++c) {
+                if (c >= P.nchan) break;
+                float2 fv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (ok[u]) fv[u] = *reinterpret_cast<const float2*>(P.f + c * n + i[u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (ok[u]) {
+                        bad |= !isfinite(fv[u].x) | !isfinite(fv[u].y);
+                        store_pair<TS>(Fo + c * P.chan_stride + o[u], fv[u].x, fv[u].y);
+                        const float f0 = to_f(from_f<TS>(fv[u].x)), f1 = to_f(from_f<TS>(fv[u].y));
+                        fmin[c] = fminf(fmin[c], fminf(f0, f1));
+                        fmax[c] = fmaxf(fmax[c], fmaxf(f0, f1));
+                    }
             }
-        },
-        [&](long long i, long long o) {
-            const float s = P.s[i];
-            const float sp = P.s_is_sp ? s : powf(s, P.p);
-            bad |= !isfinite(s) | !isfinite(sp);
-            SPo[o] = from_f<TS>(sp);
-            for (int c = 0; c < P.nchan; ++c) {
-                const float fv = P.f[c * n + i];
-                bad |= !isfinite(fv);
-                Fo[c * P.chan_stride + o] = from_f<TS>(fv);
-                track(c, to_f(from_f<TS>(fv)));
-            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) {
+                    const float sp0 = P.s_is_sp ? s[u].x : powf(s[u].x, P.p);
+                    const float sp1 = P.s_is_sp ? s[u].y : powf(s[u].y, P.p);
+                    bad |= !isfinite(s[u].x) | !isfinite(s[u].y) | !isfinite(sp0) | !isfinite(sp1);
+                    store_pair<TS>(SPo + o[u], sp0, sp1);
+                }
         });
+    } else {
+        for_each_voxel(g, one);
+    }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(P.bad, 1);
     // range of f per channel: warp, then block, then one atomic per block
     __shared__ float s_min[kMaxChan][8], s_max[kMaxChan][8];
@@ -96,23 +118,32 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
     TS* Xo = (TS*)P.x_out + g.off;
     float part = 0.f;
     int bad = 0;
-    for_each_voxel_pair(
-        g, aligned8(P.x),
-        [&](long long i, long long o) {
-            const float2 xv = *reinterpret_cast<const float2*>(P.x + i);
-            const float x0 = to_f(from_f<TS>(xv.x)), x1 = to_f(from_f<TS>(xv.y));   // as stored
-            bad |= !isfinite(x0) | !isfinite(x1);
-            store_pair<TS>(Xo + o, xv.x, xv.y);
-            part = fmaf(x0, x0, part);
-            part = fmaf(x1, x1, part);
-        },
-        [&](long long i, long long o) {
+    if (aligned8(P.x) && pair_batch_ok(g)) {
+        constexpr int U = 4;
+        for_each_pair_batch<U>(g, [&](const long long (&i)[U], const long long (&o)[U], const bool (&ok)[U]) {
+            float2 xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) xv[u] = *reinterpret_cast<const float2*>(P.x + i[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) {
+                    const float x0 = to_f(from_f<TS>(xv[u].x)), x1 = to_f(from_f<TS>(xv[u].y));   // as stored
+                    bad |= !isfinite(x0) | !isfinite(x1);
+                    store_pair<TS>(Xo + o[u], xv[u].x, xv[u].y);
+                    part = fmaf(x0, x0, part);
+                    part = fmaf(x1, x1, part);
+                }
+        });
+    } else {
+        for_each_voxel(g, [&](long long i, long long o) {
             const TS xs = from_f<TS>(P.x[i]);
             const float xv = to_f(xs);
             bad |= !isfinite(xv);
             Xo[o] = xs;
             part = fmaf(xv, xv, part);
         });
+    }
     bad = __syncthreads_or(bad);
     __shared__ double sh[32];
     __shared__ int s_last;
@@ -128,10 +159,10 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
         s_last = (prev + 1u == gridDim.x);
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
-    double xx = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) xx += __ldcg(&P.partials[b]);
+    const double xx = block_sum_partials(P.partials, (int)gridDim.x);
+    if (threadIdx.x != 0) return;
     *P.counter = 0u;
     VState st;
     st.tol = P.tol;
@@ -169,24 +200,37 @@ __global__ void __launch_bounds__(256) finish_kernel(const __grid_constant__ Fin
         const bool vec = ((unsigned long long)P.out & 15ull) == 0;
         const long long n4 = vec ? n / 4 : 0;
         float4* o4 = reinterpret_cast<float4*>(P.out);
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
-             i += (long long)gridDim.x * blockDim.x) {
-            float4 v = o4[i];
-            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
-            o4[i] = v;
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        constexpr int U = 4;   // U float4 loads in flight per thread before the stores
+        for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n4; j += U * stride) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u * stride < n4) v[u] = o4[j + u * stride];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (j + u * stride < n4) {
+                    v[u].x *= sc; v[u].y *= sc; v[u].z *= sc; v[u].w *= sc;
+                    o4[j + u * stride] = v[u];
+                }
         }
-        for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x)
+        for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
             P.out[i] = P.out[i] * sc;
+    } else if (aligned8(P.out) && pair_batch_ok(g)) {
+        constexpr int U = 4;
+        for_each_pair_batch<U>(g, [&](const long long (&i)[U], const long long (&o)[U], const bool (&ok)[U]) {
+            float2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u]) v[u] = load_pair<TS>(src + o[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (ok[u])
+                    *reinterpret_cast<float2*>(P.out + i[u]) =
+                        make_float2((float)(st.scale * (double)v[u].x), (float)(st.scale * (double)v[u].y));
+        });
     } else {
-        for_each_voxel_pair(
-            g, aligned8(P.out),
-            [&](long long i, long long o) {
-                const float2 v = load_pair<TS>(src + o);
-                *reinterpret_cast<float2*>(P.out + i) =
-                    make_float2((float)(st.scale * (double)v.x), (float)(st.scale * (double)v.y));
-            },
-            [&](long long i, long long o) { P.out[i] = (float)(st.scale * (double)to_f(src[o])); });
+        for_each_voxel(g, [&](long long i, long long o) { P.out[i] = (float)(st.scale * (double)to_f(src[o])); });
     }
 }
 

@@ -139,26 +139,40 @@ __device__ __forceinline__ void for_each_voxel(const VideoGeom& g, Fn&& fn) {
     }
 }
 
-// The same visit two columns at a time when the rows hold an even number of
-// voxels and the caller's arrays are 8-byte aligned: (i, i + 1) and
-// (o, o + 1) are then aligned pairs (pitch is a multiple of 8, every video
-// 256-byte aligned).  fn2(i, o) handles a pair; otherwise fn1 runs per voxel.
-template <typename Fn2, typename Fn1>
-__device__ __forceinline__ void for_each_voxel_pair(const VideoGeom& g, bool pairs_ok, Fn2&& fn2, Fn1&& fn1) {
-    if (!pairs_ok || (g.w & 1)) {
-        for_each_voxel(g, fn1);
-        return;
-    }
-    const int rows = g.nf * g.h, half_w = g.w >> 1;
-    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const int t = r / g.h, y = r - t * g.h;
-        const long long src = (long long)r * g.w;
-        const long long dst = (long long)t * g.plane + (long long)y * g.pitch;
-        for (int x2 = threadIdx.x; x2 < half_w; x2 += blockDim.x) fn2(src + 2 * x2, dst + 2 * x2);
+__device__ __forceinline__ bool aligned8(const void* p) { return ((unsigned long long)p & 7ull) == 0; }
+
+// Column pairs of one video (w even) U at a time per thread: pair k covers
+// the contiguous index i = 2k and the pitched offset o of row r = k / (w/2)
+// (one 32-bit division per pair).  The grid strides over the pairs and a
+// thread takes k0, k0 + S, ..., k0 + (U-1) S (S = the grid's threads), so each
+// u is a coalesced sweep and a kernel can issue its U loads before any store
+// (U x 8 bytes in flight per thread and array: enough to cover the HBM
+// latency with eight 256-thread blocks per SM).  fn(i, o, ok) gets the U
+// offsets and which of them lie inside the video.
+template <int U, typename Fn>
+__device__ __forceinline__ void for_each_pair_batch(const VideoGeom& g, Fn&& fn) {
+    const unsigned npairs = (unsigned)(g.n >> 1), hw = (unsigned)(g.w >> 1);
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < npairs; k0 += U * stride) {
+        long long i[U], o[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const unsigned k = k0 + (unsigned)u * stride;
+            ok[u] = k < npairs && k >= k0;   // (k >= k0: no wrap-around)
+            const unsigned r = k / hw;
+            i[u] = 2ll * k;
+            o[u] = (long long)r * g.pitch + 2ll * (k - r * hw);
+        }
+        fn(i, o, ok);
     }
 }
 
-__device__ __forceinline__ bool aligned8(const void* p) { return ((unsigned long long)p & 7ull) == 0; }
+// Whether for_each_pair_batch covers the video: even rows and a pair count
+// that fits its 32-bit indices.
+__device__ __forceinline__ bool pair_batch_ok(const VideoGeom& g) {
+    return (g.w & 1) == 0 && (g.n >> 1) + 8ll * gridDim.x * blockDim.x < (1ll << 32);
+}
 
 // two adjacent values of a storage array (8 / 4 / 4 bytes, aligned)
 template <typename T> __device__ __forceinline__ void store_pair(T* p, float a, float b);
@@ -208,6 +222,27 @@ __device__ __forceinline__ void warp_flush(float (&p)[kRed], double (&acc)[kRed]
         if ((threadIdx.x & 31) == 0) acc[c] += (double)s;
         p[c] = 0.f;
     }
+}
+
+// Fixed-order FP64 sum of n per-block partials (read through L2, written by
+// other blocks of the grid before their arrival), by the whole block: each
+// thread sums a strided subset, then halving folds in shared memory.  Every
+// thread of the block calls it (blockDim.x <= 256) and gets the sum.
+__device__ inline double block_sum_partials(const double* partials, int n) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += __ldcg(&partials[b]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int m = blockDim.x; m > 1;) {
+        const int h = (m + 1) / 2;
+        if ((int)threadIdx.x < m - h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+        m = h;
+    }
+    const double tot = red[0];
+    __syncthreads();   // red may be reused
+    return tot;
 }
 
 // Block-wide FP64 sum of lane-0 accumulators, result valid in thread 0.
