@@ -814,7 +814,7 @@ def main():
     ap.add_argument("--sweep-sparse", action="store_true",
                     help="with --sweep: also time the explicit sparse matrix (GPU, host) and host Lanczos")
     ap.add_argument("--sweep-flags", type=int, default=0,
-                    help="context flags for --sweep (8: any-radius kernel, 16: autotune)")
+                    help="context flags for --sweep (8: force the any-radius kernel)")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)

@@ -73,7 +73,7 @@ typedef struct {
     double alpha;            /* weight of the pairwise feature term, >= 0 */
     double p;                /* unary exponent: sp = S^p, >= 0 */
     int32_t storage;         /* sfseg_dtype */
-    int32_t flags;           /* SFSEG_* flags above */
+    int32_t flags;           /* SFSEG_* flags above; any other bit is rejected (EINVAL) */
     int32_t nchan;           /* pairwise feature channels C (Eq. 9), 1 <= C <= 4; d_f is [C][nf][h][w].
                               * M_ij = sp_i sp_j sum_c [1 - alpha (f_ci - f_cj)^2] G_ij, evaluated
                               * with C + 2 convolutions.  C > 1 runs on the any-radius step kernel;

@@ -130,6 +130,8 @@ static sfseg_status validate(const sfseg_params* p) {
         return fail(nullptr, SFSEG_EINVAL, "p must be finite and >= 0");
     if (p->storage < 0 || p->storage > 2)
         return fail(nullptr, SFSEG_EINVAL, "storage %d is not an sfseg_dtype", p->storage);
+    if (p->flags & ~(SFSEG_S_IS_SP | SFSEG_NO_GRAPH | SFSEG_RECORD | SFSEG_GENERIC))
+        return fail(nullptr, SFSEG_EINVAL, "flags 0x%x: unknown bits", (unsigned)p->flags);
     if (p->nchan < 1 || p->nchan > 8)
         return fail(nullptr, SFSEG_EINVAL, "nchan %d outside [1, 8]", p->nchan);
     if (p->nchan > kMaxChan)

@@ -46,7 +46,8 @@ def test_default_params_and_status_strings(lib):
 
 @pytest.mark.parametrize("field,value", [("rx", -1), ("ry", 17), ("rt", 9), ("sigma_t", 0.0),
                                          ("alpha", -1.0), ("p", float("nan")), ("storage", 3),
-                                         ("nf", 0), ("w", -5), ("nchan", 0)])
+                                         ("nf", 0), ("w", -5), ("nchan", 0), ("flags", 16),
+                                         ("flags", -1)])
 def test_create_rejects_bad_params(lib, field, value):
     """Validation happens on the host before any device call."""
     p = sf.sfseg_default_params(4, 8, 8)
