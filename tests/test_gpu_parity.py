@@ -224,3 +224,50 @@ def test_specialised_kernel_matches_oracle_and_generic(cuda_device, shape, radii
     assert np.array_equal(x, x2)                       # deterministic
     np.testing.assert_allclose(tr["rayleigh"], ref["rayleigh"], rtol=1e-6)
     np.testing.assert_allclose(tr["residual"], ref["residual"], rtol=1e-4)
+
+
+def test_batched_bf16_equals_single_runs_and_oracle(cuda_device):
+    """BF16 storage in the batched launch (the batched form runs FP32 and
+    BF16): each video equals its own single-video BF16 run, and its x^K is
+    within the low-precision bar of the oracle fed the same rounded operands."""
+    import torch
+    shapes = [(6, 30, 70), (4, 48, 33), (8, 20, 128)]
+    rng = np.random.default_rng(21)
+    fs = [rng.random(s, dtype=np.float32) for s in shapes]
+    radii, sig = (2, 4, 4), (1.5, 2.5, 2.5)
+    eng = sf.SFSeg(batch_shapes=shapes, radii=radii, sigmas=sig, alpha=1.0, p=0.1, storage="bf16")
+    xs = [to_dev(f) for f in fs]
+    eng.power_iterate_batched([to_dev(f) for f in fs], [to_dev(f) for f in fs], xs, 5)
+    torch.cuda.synchronize()
+    eng.close()
+    for f, xb in zip(fs, xs):
+        x1, _, st, _ = gpu_power(f, f, 5, radii, sig, 1.0, 0.1, storage="bf16")
+        assert st == sf.SFSEG_OK
+        assert rel_l2(xb.cpu().numpy(), x1) < 1e-5
+        ref = oracle_power(f, f, 5, radii, sig, 1.0, 0.1, storage="bf16")
+        assert rel_l2(xb.cpu().numpy(), ref["x"]) < TOL_LOWP
+
+
+def test_batched_many_small_videos(cuda_device):
+    """More videos than CTAs (one voxel, single rows and columns, a video
+    wider than one tile), in one launch per step: each equals its own run."""
+    import torch
+    rng = np.random.default_rng(5)
+    shapes = [(1, 1, 1), (1, 1, 9), (3, 1, 5), (2, 7, 1)]
+    shapes += [tuple(int(v) for v in rng.integers(1, 12, size=3)) for _ in range(200)]
+    shapes += [(12, 40, 300)]
+    fs = [0.9 * rng.random(s, dtype=np.float32) + 0.05 for s in shapes]
+    radii, sig = (2, 5, 5), (1.5, 3.0, 3.0)
+    eng = sf.SFSeg(batch_shapes=shapes, radii=radii, sigmas=sig, alpha=1.0, p=0.1)
+    xs = [to_dev(f) for f in fs]
+    eng.power_iterate_batched([to_dev(f) for f in fs], [to_dev(f) for f in fs], xs, 4)
+    torch.cuda.synchronize()
+    eng.close()
+    for k in list(range(8)) + [len(shapes) - 1]:
+        x1, _, _, _ = gpu_power(fs[k], fs[k], 4, radii, sig, 1.0, 0.1)
+        assert rel_l2(xs[k].cpu().numpy(), x1) < 1e-6, (k, shapes[k])
+    one = xs[0].cpu().numpy()
+    assert one.shape == (1, 1, 1) and abs(float(one.ravel()[0]) - 1.0) < 1e-6   # x = 1 for one voxel
+    for k in range(len(shapes)):
+        x = xs[k].cpu().numpy().astype(np.float64)
+        assert abs(np.linalg.norm(x) - 1.0) < 1e-5 and x.min() >= -1e-7, (k, shapes[k])
