@@ -12,7 +12,7 @@
 //
 // Per segment the CTA streams frames, with two warp roles that overlap:
 //   load    one thread issues three TMA 3D box loads (x, sp, f) of the tile
-//           plus its halo (128 x (12 + 2 RY)) into a ring of RT + 2 + LA
+//           plus its halo (128 x (12 + 2 RY)) into a ring of RT + NYB + LA
 //           shared-memory stages (zero fill outside the volume = the zero
 //           padding of Eq. 7's convolutions), LA frames ahead, completion on
 //           an mbarrier per stage;
@@ -20,7 +20,8 @@
 //           a0 = sp x, a1 = f a0, a2 = f a1 and the vertical taps in
 //           registers, every channel packed over the column pair (FMUL2 /
 //           FFMA2); (a0, a1) are stored interleaved per column in a swizzled
-//           plane, a2 in its own plane, double-buffered; FULL mbarrier;
+//           plane, a2 in its own plane, in NYB buffers (2 for FP32
+//           storage, 4 for 2-byte storage); FULL mbarrier;
 //   x-pass  warps 4..15 ("B"): warp w owns output row w - 4, lanes 0..27 four
 //           output columns each, windows read straight from shared memory;
 //           (a0, a1) filtered with packed FMAs (a1's taps carry the factor
@@ -180,14 +181,17 @@ struct Cfg {
     static constexpr int ROWS = TY + 2 * RY;                  // input rows per tile
     static constexpr int IN_ROWS = TROWS + 2 * RY;            // input rows per task
     static constexpr int NR = 2 * RT + 1;                     // temporal taps
-    static constexpr int NS = RT + 2 + LA;                    // stages (see the stage-reuse note)
+    // y-pass output buffers: the x-pass warps may trail the y-pass by NYB - 1
+    // frames (with 2-byte storage the stages are small enough for four)
+    static constexpr int NYB = sizeof(TS) == 4 ? 2 : 4;
+    static constexpr int NS = RT + NYB + LA;                  // stages (see the stage-reuse note)
     static constexpr int BOX_BYTES = ROWS * BOXW * (int)sizeof(TS);
     static constexpr int ARR = (BOX_BYTES + 127) / 128 * 128; // one array of a stage
     static constexpr int STAGE = 3 * ARR;
     static constexpr int YBC = TY * YBW * 4;                  // one channel of one Yb buffer
     static constexpr int YB = 3 * YBC;                        // one Yb buffer (3 channels)
-    static constexpr int NBAR = NS + 4;                       // stages, FULL[2], EMPTY[2]
-    static constexpr int SMEM = NS * STAGE + 2 * YB + NBAR * 8 + 128;
+    static constexpr int NBAR = NS + 2 * NYB;                 // stages, FULL[NYB], EMPTY[NYB]
+    static constexpr int SMEM = NS * STAGE + NYB * YB + NBAR * 8 + 128;
     static_assert(NTA <= NA_WARPS * 32 && TY % NGRP == 0, "y-pass tasks must tile the rows");
     static_assert(RX <= XPAD && SC0 >= 0, "x radius exceeds the halo pad");
     static_assert(NS * STAGE >= NT * kRed * 8, "finalize scratch must fit in the stages");
@@ -282,18 +286,18 @@ __device__ __forceinline__ void xpass_abc(const float* row_ab, const float* row_
 }
 
 // Warp roles.  Warps 0..3 ("A"): the elected thread issues the TMA loads LA
-// frames ahead; all of them run the y-pass of frame p into Yb[vc % 2] (vc
+// frames ahead; all of them run the y-pass of frame p into Yb[vc % NYB] (vc
 // counts the valid frames of the segment), then each A warp arrives once on
 // the FULL mbarrier of that buffer.  Warps 4.. ("B", one output row each):
 // each waits on FULL on its own (the B warps are not coupled to each other),
 // x-pass and temporal ring of the three channels, combine of frame p - RT
 // (its x, sp, f from the frame's stage), store, then arrives once on EMPTY.
 // A waits until all B warps have arrived on EMPTY of a buffer before refilling
-// it, so A runs at most two frames ahead of B's completed work.
-// Stage reuse: with NS = RT + 2 + LA stages and loads LA frames ahead, the
+// it, so A runs at most NYB frames ahead of B's completed work.
+// Stage reuse: with NS = RT + NYB + LA stages and loads LA frames ahead, the
 // load of frame p + LA (issued at frame p, after A's EMPTY wait) overwrites
-// frame p - RT - 2, whose last reader (B's combine of that frame, at B's
-// frame p - 2) arrived on EMPTY before A passed that wait.
+// frame p - RT - NYB, whose last reader (B's combine of that frame, at B's
+// frame p - NYB) arrived on EMPTY before A passed that wait.
 template <int RT, int RY, int RX, typename TS, bool AUX, bool MC>
 __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant__ StepParams P) {
     using C = Cfg<RT, RY, RX, TS>;
@@ -301,7 +305,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* stages = smem;
     float* yb = reinterpret_cast<float*>(smem + NS * C::STAGE);        // [2][3][TY][YBW]
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + NS * C::STAGE + 2 * C::YB);
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + NS * C::STAGE + C::NYB * C::YB);
     __shared__ float s_scale, s_gain, s_shift;
     __shared__ int s_skip, s_abort;
     __shared__ __align__(8) unsigned long long s_never;   // an mbarrier nothing arrives on (fault injection)
@@ -312,10 +316,10 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P.maps);
 
     unsigned long long* full = bars + NS;       // [2], NA_WARPS arrivals per phase
-    unsigned long long* empty = bars + NS + 2;  // [2], NB_WARPS arrivals per phase
+    unsigned long long* empty = bars + NS + C::NYB;  // [NYB], NB_WARPS arrivals per phase
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < C::NYB; ++b) {
             mbar_init(smem_u32(&full[b]), NA_WARPS);
             mbar_init(smem_u32(&empty[b]), NB_WARPS);
         }
@@ -397,8 +401,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                 for (int q = 0; q < LA && q < n_valid; ++q) issue(p_first + q);
             for (int vc = 0; vc < n_valid; ++vc) {
                 const int p = p_first + vc;
-                const int b = vc & 1;
-                const unsigned n = (unsigned)(vc >> 1);
+                const int b = (int)((unsigned)vc % C::NYB);
+                const unsigned n = (unsigned)vc / C::NYB;
                 if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u, &s_abort))
                     give_up(v);
                 if (tid == 0 && !s_abort && vc + LA < n_valid) issue(p + LA);
@@ -478,14 +482,14 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             auto frame = [&](auto phase) {
                 constexpr int U = decltype(phase)::value;
                 const bool valid = (tin >= 0 && tin < g.nf);
-                const int b = vc & 1;
+                const int b = (int)((unsigned)vc % C::NYB);
                 float2 pab[4];
                 float pc[4];
                 if (valid) {
                     if (P.inject_timeout && brow == 0 && vc == 0 &&
                         !mbar_wait(smem_u32(&s_never), 0u, &s_abort))
                         give_up(v);
-                    if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ (unsigned)(vc >> 1)) & 1u, &s_abort))
+                    if (!mbar_wait(smem_u32(&full[b]), ((fullbase >> b) ^ ((unsigned)vc / C::NYB)) & 1u, &s_abort))
                         give_up(v);
                     const float* yc = yb + b * 3 * TY * YBW;
                     // lanes 28..31 have no outputs: give them lane 27's window so
@@ -608,9 +612,9 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             __syncthreads();
             return;
         }
-        // buffer b was used (n_valid + 1 - b) / 2 times: FULL and EMPTY advanced
-        for (int b = 0; b < 2; ++b) {
-            const unsigned uses = (unsigned)((n_valid + 1 - b) / 2);
+        // buffer b was used ceil((n_valid - b) / NYB) times: FULL and EMPTY advanced
+        for (int b = 0; b < C::NYB; ++b) {
+            const unsigned uses = (unsigned)((n_valid - b + C::NYB - 1) / C::NYB);
             fullbase ^= (uses & 1u) << b;
             emptybase ^= (uses & 1u) << b;
         }
