@@ -169,12 +169,13 @@ def rank_video_index(rank):
     return int(rank)
 
 
-def cpu_baseline(wl, seconds_hint: float = 15.0):
+def cpu_baseline(wl, frames=None):
     """The FP64 oracle as it stands, on this host's cores, over a bounded
     sample of the workload, in the workload's unit (voxel-iterations / s):
-    the video (all its frames) and 4 power steps; for the batch its first
-    video; for the differentiable form 8 frames, 4 steps forward plus the
-    oracle's reverse mode (the bench step there is forward + adjoint)."""
+    the video (all its frames, or the first `frames`) and 4 power steps; for
+    the batch its first video; for the differentiable form 8 frames, 4 steps
+    forward plus the oracle's reverse mode (the bench step there is forward +
+    adjoint)."""
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     import oracle
@@ -191,6 +192,10 @@ def cpu_baseline(wl, seconds_hint: float = 15.0):
         what = f"the {wl.w}x{wl.h}x{wl.nf} video"
     grad = wl.name.startswith("grad")
     nf_s = 8 if grad else s.shape[0]
+    if frames is not None and not grad:
+        nf_s = max(1, min(nf_s, int(frames)))
+        if nf_s < s.shape[0]:
+            what = f"the first {nf_s} frames of " + what
     sub = np.ascontiguousarray(s[:nf_s], dtype=np.float64)
     fsub = np.ascontiguousarray(f[..., :nf_s, :, :], dtype=np.float64)
     sp = oracle.unary(sub, wl.p)
@@ -214,8 +219,11 @@ def run_reference(args, wl):
         return
     steps = []
     cb = None
+    # each step samples fewer frames when many steps are asked for, so that
+    # the whole run stays within a few minutes (about 12 full-video samples)
+    frames = max(8, (wl.nf * 12) // max(1, args.warmup + args.steps))
     for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl)
+        cb = cpu_baseline(wl, frames=frames)
         steps.append(cb["value"])
     vals = steps[args.warmup:]
     value = statistics.median(vals)
