@@ -39,7 +39,9 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # ncu --set full --clock-control none -k regex:step_fast -s 10 -c 1 ...
 # python bench.py --steps 2 --warmup 1 --no-cpu-baseline).  Only workloads
 # whose kernel was captured have an entry; the others report null.
-DRAM_TRAFFIC_PER_LAUNCH = {("video_72x480x854", "f32"): 367.805696e6 + 99.330048e6}
+DRAM_TRAFFIC_PER_LAUNCH = {("video_72x480x854", "f32"): 367.805696e6 + 99.330048e6,
+                           # profiles/step_fast_bf16_video_72x480x854.md, same command with --storage bf16
+                           ("video_72x480x854", "bf16"): 181.775872e6 + 40.524288e6}
 
 
 def alu_flops_per_voxel(wl) -> int:
