@@ -63,8 +63,40 @@ enum {
     SFSEG_S_IS_SP = 1,       /* d_s already holds S^p; p is ignored */
     SFSEG_NO_GRAPH = 2,      /* launch the iteration loop eagerly (no CUDA graph) */
     SFSEG_RECORD = 4,        /* record checkpoints during power_iterate for sfseg_adjoint */
-    SFSEG_GENERIC = 8        /* force the generic (any-radius) stencil kernel */
+    SFSEG_GENERIC = 8,       /* force the generic (any-radius) stencil kernel */
+    SFSEG_FUSED = 16,        /* power_iterate runs all its steps in one launch (see below) */
+    SFSEG_AUTOTUNE = 32      /* power_iterate chooses its step path by timing (see below) */
 };
+
+/* Step paths of sfseg_power_iterate(_batched) (the loop of Algorithm 1, one
+ * power step = Eq. 7 + Eq. 8 per iteration):
+ *   SFSEG_PATH_FAST     one launch per step of the specialised kernel (radii
+ *                       (2,5,5) and (2,4,4)), replayed as a CUDA graph;
+ *   SFSEG_PATH_GENERIC  one launch per step of the any-radius kernel;
+ *   SFSEG_PATH_FUSED    all K steps in one cooperative launch: per step, the
+ *                       y and x passes of every (frame, tile) into an FP32
+ *                       scratch of three volumes (12 bytes per voxel, allocated
+ *                       by the context on first use), a grid-wide barrier, the
+ *                       t-pass, combine, reductions and norm update, a second
+ *                       barrier.  Meant for small volumes (whose fixed per-step
+ *                       launch cost dominates); one channel only; every
+ *                       barrier wait gives up after 1 s with SFSEG_ETIMEOUT.
+ * Default: FAST where the radii are specialised, else GENERIC; SFSEG_FUSED
+ * selects FUSED (SFSEG_EUNSUPPORTED for nchan > 1, with SFSEG_RECORD, or on a
+ * device without cooperative launch).  SFSEG_AUTOTUNE: the first
+ * power_iterate call on the context times each path it can run (and the fused
+ * launch at three grid sizes, when the volume has at most 8 Mi voxels) on the
+ * context's own features and x0, keeps the fastest and caches the choice per
+ * (video shapes, radii, storage, channels, device) for the process.  That
+ * first call synchronises the stream and must not be captured into a graph.
+ * Paths differ only in floating-point summation order.  sfseg_rayleigh,
+ * sfseg_apply, the binarised and the recorded iteration always run one launch
+ * per step (the GENERIC kernel when that path was chosen). */
+typedef enum {
+    SFSEG_PATH_FAST = 0,
+    SFSEG_PATH_GENERIC = 1,
+    SFSEG_PATH_FUSED = 2
+} sfseg_path;
 
 typedef struct {
     int32_t nf, h, w;        /* volume: frames x rows x cols, all >= 1 */
@@ -268,6 +300,14 @@ int32_t sfseg_plan_segments(int32_t n_videos, const int32_t* dims, int32_t n_sms
 
 /* Number of kernel launches this context issued so far (for accounting). */
 int64_t sfseg_launch_count(const sfseg_ctx* ctx);
+
+/* The step path power_iterate uses (sfseg_path; with SFSEG_AUTOTUNE, the one
+ * chosen by the first call), the CTA count of the fused launch (0 for the
+ * per-step paths) and, nullable, us_per_step[3]: the microseconds per step the
+ * autotuner measured for each path (index = sfseg_path; -1 where not timed).
+ * No device access.  Errors: EINVAL. */
+sfseg_status sfseg_get_path(const sfseg_ctx* ctx, int32_t* path, int32_t* fused_ctas,
+                            double* us_per_step);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,9 @@ SFSEG_OK, SFSEG_EINVAL, SFSEG_ENOMEM, SFSEG_ECUDA, SFSEG_EZERONORM = 0, 1, 2, 3,
 SFSEG_ENONFINITE, SFSEG_ETIMEOUT, SFSEG_EUNSUPPORTED, SFSEG_ESTATE = 5, 6, 7, 8
 SFSEG_F32, SFSEG_BF16, SFSEG_F16 = 0, 1, 2
 SFSEG_S_IS_SP, SFSEG_NO_GRAPH, SFSEG_RECORD, SFSEG_GENERIC = 1, 2, 4, 8
+SFSEG_FUSED, SFSEG_AUTOTUNE = 16, 32
+SFSEG_PATH_FAST, SFSEG_PATH_GENERIC, SFSEG_PATH_FUSED = 0, 1, 2
+PATH_NAMES = {SFSEG_PATH_FAST: "fast", SFSEG_PATH_GENERIC: "generic", SFSEG_PATH_FUSED: "fused"}
 STORAGE = {"f32": SFSEG_F32, "bf16": SFSEG_BF16, "f16": SFSEG_F16}
 
 # Every entry point declared in include/sfseg.h.
@@ -33,7 +36,7 @@ EXPORTS = (
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
     "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
     "sfseg_default_binarize", "sfseg_power_iterate_binarized", "sfseg_debug_inject_timeout",
-    "sfseg_get_warnings",
+    "sfseg_get_warnings", "sfseg_get_path",
 )
 SFSEG_WARN_NEGATIVE_M = 1
 
@@ -100,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "sfseg_default_binarize": (None, [ctypes.POINTER(sfseg_binarize)]),
         "sfseg_debug_inject_timeout": (_i32, [_vp, _i32]),
         "sfseg_get_warnings": (_i32, [_vp, ctypes.POINTER(_i32)]),
+        "sfseg_get_path": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
         "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
                                                  ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
@@ -261,6 +265,13 @@ def sfseg_plan_segments(dims, n_sms: int):
     return rows, cta
 
 
+def sfseg_get_path(ctx: int):
+    """(path, fused CTA count, [us per step measured per path or -1]) of a context."""
+    path, ctas, us = _i32(), _i32(), (_dbl * 3)()
+    _check(load_library().sfseg_get_path(ctx, ctypes.byref(path), ctypes.byref(ctas), us), ctx)
+    return path.value, ctas.value, list(us)
+
+
 # --------------------------------------------------- torch convenience wrapper
 def _stream_handle():
     import torch
@@ -389,3 +400,9 @@ class SFSeg:
 
     def launch_count(self) -> int:
         return sfseg_launch_count(self.ctx)
+
+    def path(self):
+        """{'path': 'fast'|'generic'|'fused', 'fused_ctas': n, 'tuned_us': {...}}."""
+        pth, ctas, us = sfseg_get_path(self.ctx)
+        return {"path": PATH_NAMES[pth], "fused_ctas": ctas,
+                "tuned_us": {PATH_NAMES[i]: u for i, u in enumerate(us) if u >= 0}}

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -83,6 +84,25 @@ struct sfseg_ctx {
     unsigned* d_adj_counter = nullptr;
     bool recorded = false;
     int rec_K = 0;
+    // step path of power_iterate: per-step specialised / per-step any-radius /
+    // all steps in one cooperative launch (step_fused.cu)
+    int path = SFSEG_PATH_FAST;
+    bool tune_pending = false;  // SFSEG_AUTOTUNE: choose the path at the first power_iterate
+    double tuned_us[3] = {-1.0, -1.0, -1.0};   // measured us per step of each path (-1: not timed)
+    // fused path: phase-2 runs, barrier words, scratch (allocated on first use)
+    bool fused_ok = false;      // the context can run the fused kernel
+    int fused_max = 0;          // co-resident CTAs of the fused kernel on this device
+    int fused_ctas = 0;         // CTAs of the fused launch (the plan below is built for it)
+    int fused_n_units1 = 0;
+    int fused_n_items = 0;
+    int* d_fu1 = nullptr;       // [nv + 1] phase-1 unit prefix
+    WorkItem* d_fitems = nullptr;
+    int* d_fcta_begin = nullptr;
+    int* d_fitem_begin = nullptr;
+    int* d_fvseg = nullptr;
+    double* d_fpartials = nullptr;
+    unsigned* d_fbar = nullptr; // [3]
+    float* d_pvol = nullptr;    // 3 FP32 volumes
     std::vector<int> item_begin;
     // host-side
     float gt[2 * kMaxRt + 1], gy[2 * kMaxR + 1], gx[2 * kMaxR + 1];
@@ -130,8 +150,16 @@ static sfseg_status validate(const sfseg_params* p) {
         return fail(nullptr, SFSEG_EINVAL, "p must be finite and >= 0");
     if (p->storage < 0 || p->storage > 2)
         return fail(nullptr, SFSEG_EINVAL, "storage %d is not an sfseg_dtype", p->storage);
-    if (p->flags & ~(SFSEG_S_IS_SP | SFSEG_NO_GRAPH | SFSEG_RECORD | SFSEG_GENERIC))
+    if (p->flags & ~(SFSEG_S_IS_SP | SFSEG_NO_GRAPH | SFSEG_RECORD | SFSEG_GENERIC | SFSEG_FUSED |
+                     SFSEG_AUTOTUNE))
         return fail(nullptr, SFSEG_EINVAL, "flags 0x%x: unknown bits", (unsigned)p->flags);
+    if ((p->flags & SFSEG_FUSED) && (p->flags & (SFSEG_GENERIC | SFSEG_AUTOTUNE)))
+        return fail(nullptr, SFSEG_EINVAL, "SFSEG_FUSED excludes SFSEG_GENERIC and SFSEG_AUTOTUNE");
+    if ((p->flags & (SFSEG_FUSED | SFSEG_AUTOTUNE)) && (p->flags & SFSEG_RECORD))
+        return fail(nullptr, SFSEG_EUNSUPPORTED,
+                    "SFSEG_RECORD runs the per-step kernel (no SFSEG_FUSED / SFSEG_AUTOTUNE)");
+    if ((p->flags & SFSEG_FUSED) && p->nchan != 1)
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "the fused kernel runs one channel (nchan = 1)");
     if (p->nchan < 1 || p->nchan > 8)
         return fail(nullptr, SFSEG_EINVAL, "nchan %d outside [1, 8]", p->nchan);
     if (p->nchan > kMaxChan)
@@ -157,7 +185,8 @@ static void free_ctx(sfseg_ctx* c) {
                     c->d_trace, c->d_out, c->d_cta_begin, c->d_vseg, c->d_maps,
                     c->d_gitems, c->d_gitem_begin, c->d_gpartials, c->d_rec, c->d_rrec,
                     c->d_ckpt, c->d_adj, c->d_adjc, c->d_adj_partials, c->d_adj_counter, c->d_bin,
-                    c->d_adj_misc, c->d_fmin, c->d_fmax};
+                    c->d_adj_misc, c->d_fmin, c->d_fmax, c->d_fu1, c->d_fitems, c->d_fcta_begin,
+                    c->d_fitem_begin, c->d_fvseg, c->d_fpartials, c->d_fbar, c->d_pvol};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -294,6 +323,100 @@ static const char* encode_maps(sfseg_ctx* c, CUtensorMap* maps) {
         }
     }
     return nullptr;
+}
+
+// Work plan of the fused kernel for G CTAs.  Phase 1: per video, frames x
+// 32x16 tiles (unit1_begin = prefix over videos; CTAs stride over them).
+// Phase 2: per video, frames x chunks of fused_rows2(w) rows, laid end to end
+// over all videos and cut into G equal contiguous ranges; a range's units of
+// one video form one item (a run that arrives once at the finalize).
+struct FusedPlan {
+    std::vector<int> unit1_begin;
+    std::vector<WorkItem> items;
+    std::vector<int> cta_begin, item_begin, vseg;
+};
+
+static long long fused_units2(const VideoGeom& g) {
+    const int rows = fused_rows2(g.w);
+    return (long long)g.nf * ((g.h + rows - 1) / rows);
+}
+
+static void build_fused_plan(const std::vector<VideoGeom>& geo, int G, FusedPlan* fp) {
+    int tx, ty, nt;
+    fused_tile(&tx, &ty, &nt);
+    fp->unit1_begin.assign(1, 0);
+    for (const VideoGeom& g : geo)
+        fp->unit1_begin.push_back(fp->unit1_begin.back() +
+                                  g.nf * ((g.h + ty - 1) / ty) * ((g.w + tx - 1) / tx));
+    std::vector<long long> u2b(1, 0);
+    for (const VideoGeom& g : geo) u2b.push_back(u2b.back() + fused_units2(g));
+    const long long U2 = u2b.back();
+    fp->items.clear();
+    fp->cta_begin.assign(G + 1, 0);
+    int v = 0;
+    for (int c = 0; c < G; ++c) {
+        fp->cta_begin[c] = (int)fp->items.size();
+        long long a = U2 * c / G;
+        const long long b = U2 * (c + 1) / G;
+        while (a < b) {
+            while (u2b[v + 1] <= a) ++v;
+            const long long e = b < u2b[v + 1] ? b : u2b[v + 1];
+            WorkItem it{};
+            it.video = v;
+            it.t0 = (int)(a - u2b[v]);
+            it.t1 = (int)(e - u2b[v]);
+            fp->items.push_back(it);
+            a = e;
+        }
+    }
+    fp->cta_begin[G] = (int)fp->items.size();
+    fp->vseg.clear();
+    fp->item_begin.clear();
+    for (int w = 0; w < (int)geo.size(); ++w) {
+        fp->item_begin.push_back((int)fp->vseg.size());
+        for (int i = 0; i < (int)fp->items.size(); ++i)
+            if (fp->items[i].video == w) fp->vseg.push_back(i);
+    }
+    fp->item_begin.push_back((int)fp->vseg.size());
+}
+
+// CTAs worth launching: no more than the resident maximum, nor than the
+// larger phase's unit count.
+static int fused_default_ctas(const sfseg_ctx* c) {
+    int tx, ty, nt;
+    fused_tile(&tx, &ty, &nt);
+    long long u1 = 0, u2 = 0;
+    for (const VideoGeom& g : c->geo) {
+        u1 += (long long)g.nf * ((g.h + ty - 1) / ty) * ((g.w + tx - 1) / tx);
+        u2 += fused_units2(g);
+    }
+    long long n = u1 > u2 ? u1 : u2;
+    if (n > c->fused_max) n = c->fused_max;
+    return n < 1 ? 1 : (int)n;
+}
+
+// Upload the fused plan for G CTAs (host-synchronous; never during a capture).
+static cudaError_t upload_fused_plan(sfseg_ctx* c, int G) {
+    FusedPlan fp;
+    build_fused_plan(c->geo, G, &fp);
+    cudaError_t e = cudaMemcpy(c->d_fu1, fp.unit1_begin.data(), sizeof(int) * fp.unit1_begin.size(),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_fitems, fp.items.data(), sizeof(WorkItem) * fp.items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_fcta_begin, fp.cta_begin.data(), sizeof(int) * fp.cta_begin.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_fitem_begin, fp.item_begin.data(), sizeof(int) * fp.item_begin.size(),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !fp.vseg.empty())
+        e = cudaMemcpy(c->d_fvseg, fp.vseg.data(), sizeof(int) * fp.vseg.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        c->fused_ctas = G;
+        c->fused_n_units1 = fp.unit1_begin.back();
+        c->fused_n_items = (int)fp.items.size();
+    }
+    return e;
 }
 
 static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* dims, bool batched,
@@ -445,6 +568,33 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         e = cudaMemcpy(c->d_gitem_begin, gitem_begin.data(), sizeof(int) * gitem_begin.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = setup_step_generic(prm->rt, prm->ry, prm->rx);
+    if (e == cudaSuccess && prm->nchan == 1 && !(prm->flags & SFSEG_RECORD)) {
+        // fused path: its plan arrays hold the largest plan (one item per CTA
+        // and video boundary); the scratch volumes are allocated on first use
+        e = setup_step_fused(prm->storage, prm->ry, prm->rx, &c->fused_max);
+        if (e == cudaSuccess && c->fused_max > 0) {
+            const size_t cap = (size_t)c->fused_max + nv;
+            e = cudaMalloc((void**)&c->d_fu1, sizeof(int) * (nv + 1));
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fitems, sizeof(WorkItem) * cap);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fcta_begin, sizeof(int) * (c->fused_max + 1));
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fitem_begin, sizeof(int) * (nv + 1));
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fvseg, sizeof(int) * cap);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fpartials, sizeof(double) * kRed * cap);
+            if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_fbar, sizeof(unsigned) * 3);
+            if (e == cudaSuccess) e = upload_fused_plan(c, fused_default_ctas(c));
+            if (e == cudaSuccess) c->fused_ok = true;
+        }
+    }
+    c->path = c->fast ? SFSEG_PATH_FAST : SFSEG_PATH_GENERIC;
+    if (e == cudaSuccess && (prm->flags & SFSEG_FUSED)) {
+        if (!c->fused_ok) {
+            fail(nullptr, SFSEG_EUNSUPPORTED, "SFSEG_FUSED: this device has no cooperative launch");
+            free_ctx(c);
+            return SFSEG_EUNSUPPORTED;
+        }
+        c->path = SFSEG_PATH_FUSED;
+    }
+    c->tune_pending = (prm->flags & SFSEG_AUTOTUNE) != 0;
     if (e == cudaSuccess && c->fast) {
         e = setup_step_fast(prm->rt, prm->ry, prm->rx, prm->storage);
         if (e == cudaSuccess)
@@ -542,7 +692,16 @@ static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, 
         c->inject_steps -= 1;
     }
     c->launches += 1;
-    if (c->fast && c->prm.nchan > 1) {
+    const bool fast = c->fast && c->path != SFSEG_PATH_GENERIC;
+    if (!fast) {   // the any-radius kernel on its own tile plan
+        P.items = c->d_gitems;
+        P.item_begin = c->d_gitem_begin;
+        P.partials = c->d_gpartials;
+        P.vseg = nullptr;
+        P.n_items = c->g_n_items;
+        return launch_step_generic(c->prm.storage, P, c->g_n_items, s);
+    }
+    if (c->prm.nchan > 1) {
         // Eq. 9 as one pass per channel: every pass adds its M_c x to the
         // partial sum in the step's output buffer; the last pass also reduces
         // (and writes the caller's buffer in final mode)
@@ -564,8 +723,42 @@ static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, 
         c->launches += C - 1;
         return cudaSuccess;
     }
-    if (c->fast) return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
-    return launch_step_generic(c->prm.storage, P, c->n_items, s);
+    return launch_step_fast(c->prm.storage, P, c->n_ctas, s);
+}
+
+// All n power steps of a call in one cooperative launch (step_fused.cu).  The
+// last step writes the caller's FP32 buffers when final_mode is set (the
+// pointer table d_out must hold them).
+static sfseg_status run_fused(sfseg_ctx* c, int n, bool final_mode, cudaStream_t s) {
+    if (n <= 0) return SFSEG_OK;
+    if (!c->d_pvol)
+        CUDA_OR(c, cudaMalloc((void**)&c->d_pvol, sizeof(float) * 3 * (size_t)c->total));
+    FusedParams F{};
+    F.S = step_params(c, 0, final_mode, true);
+    F.S.items = c->d_fitems;
+    F.S.cta_begin = c->d_fcta_begin;
+    F.S.item_begin = c->d_fitem_begin;
+    F.S.vseg = c->d_fvseg;
+    F.S.partials = c->d_fpartials;
+    F.S.n_items = c->fused_n_items;
+    if (c->inject_steps > 0) {
+        F.S.inject_timeout = 1;
+        c->inject_steps = 0;
+    }
+    F.buf0 = c->xa;
+    F.buf1 = c->xb;
+    F.pvol = c->d_pvol;
+    F.total = c->total;
+    F.unit1_begin = c->d_fu1;
+    F.n_units1 = c->fused_n_units1;
+    F.n_videos = c->nv;
+    F.n_steps = n;
+    F.final_mode = final_mode ? 1 : 0;
+    F.bar = c->d_fbar;
+    CUDA_OR(c, cudaMemsetAsync(c->d_fbar, 0, sizeof(unsigned) * 3, s));
+    CUDA_OR(c, launch_step_fused(c->prm.storage, F, c->fused_ctas, s));
+    c->launches += 1;
+    return SFSEG_OK;
 }
 
 // Steps [0, n) that store into the internal ping-pong buffers: one CUDA
@@ -733,6 +926,112 @@ static sfseg_status iterate_record(sfseg_ctx* c, const float* d_x_in, float* d_x
     return SFSEG_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+// SFSEG_AUTOTUNE: at the first power_iterate the context times every step path
+// it can run on its own features and x0 (the per-step specialised kernel, the
+// per-step any-radius kernel, and the fused launch with the default, half and
+// quarter CTA count when the volume is small enough for its scratch to stay in
+// L2), and keeps the fastest.  The choice is cached per (video shapes, radii,
+// storage, channels, device) for the process, so later contexts of the same
+// shape class skip the timing.  Every candidate computes the same operator;
+// results differ only in summation order.
+static constexpr long long kFusedTuneMaxVoxels = 8ll << 20;   // scratch 3 x 4 B x N <= 96 MiB
+static constexpr int kTuneSteps = 6;
+
+struct TuneChoice { int path, ctas; double us[3]; };
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune_cache;
+
+static std::string tune_key(const sfseg_ctx* c) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::string k = std::to_string(dev) + ":" + std::to_string(c->prm.rt) + "," + std::to_string(c->prm.ry) +
+                    "," + std::to_string(c->prm.rx) + ":" + std::to_string(c->prm.storage) + ":" +
+                    std::to_string(c->prm.nchan) + ":" + std::to_string(c->fast ? 1 : 0);
+    for (const VideoGeom& g : c->geo)
+        k += ":" + std::to_string(g.nf) + "x" + std::to_string(g.h) + "x" + std::to_string(g.w);
+    return k;
+}
+
+static void drop_graphs(sfseg_ctx* c) {   // captured graphs belong to the path they were taken on
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
+static sfseg_status set_path(sfseg_ctx* c, int path, int ctas) {
+    if (path != c->path) drop_graphs(c);
+    c->path = path;
+    if (path == SFSEG_PATH_FUSED && ctas != c->fused_ctas) CUDA_OR(c, upload_fused_plan(c, ctas));
+    return SFSEG_OK;
+}
+
+static sfseg_status autotune(sfseg_ctx* c, const float* const* d_x_in, cudaStream_t s) {
+    c->tune_pending = false;
+    const std::string key = tune_key(c);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            memcpy(c->tuned_us, it->second.us, sizeof c->tuned_us);
+            return set_path(c, it->second.path, it->second.ctas);
+        }
+    }
+    struct Cand { int path, ctas; };
+    std::vector<Cand> cands;
+    if (c->fast) cands.push_back({SFSEG_PATH_FAST, 0});
+    cands.push_back({SFSEG_PATH_GENERIC, 0});
+    if (c->fused_ok && c->total <= kFusedTuneMaxVoxels) {
+        const int g0 = fused_default_ctas(c);
+        for (int g : {g0, (g0 + 1) / 2, (g0 + 3) / 4})
+            if (g >= 1 && (cands.back().path != SFSEG_PATH_FUSED || cands.back().ctas != g))
+                cands.push_back({SFSEG_PATH_FUSED, g});
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_OR(c, cudaEventCreate(&e0));
+    CUDA_OR(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    Cand pick = cands[0];
+    double us_path[3] = {-1.0, -1.0, -1.0};
+    sfseg_status st = SFSEG_OK;
+    for (const Cand& cd : cands) {
+        if ((st = set_path(c, cd.path, cd.ctas)) != SFSEG_OK) break;
+        double us = 0.0;
+        for (int rep = 0; rep < 2 && st == SFSEG_OK; ++rep) {   // rep 0 warms up (graph capture, scratch)
+            cudaEventRecord(e0, s);
+            for (int v = 0; v < c->nv && st == SFSEG_OK; ++v) st = prep_x(c, v, d_x_in[v], false, 0.0, s);
+            if (st != SFSEG_OK) break;
+            st = cd.path == SFSEG_PATH_FUSED ? run_fused(c, kTuneSteps, false, s) : run_steps(c, kTuneSteps, s);
+            if (st != SFSEG_OK) break;
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = fail(c, SFSEG_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+                break;
+            }
+            us = 1000.0 * ms / kTuneSteps;
+        }
+        if (st != SFSEG_OK) break;
+        if (us_path[cd.path] < 0.0 || us < us_path[cd.path]) us_path[cd.path] = us;
+        if (us < best) {
+            best = us;
+            pick = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SFSEG_OK) return st;
+    memcpy(c->tuned_us, us_path, sizeof us_path);
+    st = set_path(c, pick.path, pick.ctas);
+    if (st != SFSEG_OK) return st;
+    drop_graphs(c);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneChoice tc{pick.path, pick.ctas, {us_path[0], us_path[1], us_path[2]}};
+    g_tune_cache[key] = tc;
+    return SFSEG_OK;
+}
+
 static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float* const* d_x,
                                  int K, double tol, int32_t* iters_done, cudaStream_t s) {
     if (K < 0) return fail(c, SFSEG_EINVAL, "n_iters must be >= 0");
@@ -755,17 +1054,30 @@ static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float
         return st;
     }
     c->recorded = false;
+    if (c->tune_pending) {
+        st = autotune(c, d_x_in, s);
+        if (st != SFSEG_OK) return st;
+    }
     for (int v = 0; v < c->nv; ++v) {
         st = prep_x(c, v, d_x_in[v], false, tol, s);
         if (st != SFSEG_OK) return st;
     }
     const bool final_mode = (K > 0 && tol == 0.0);
-    st = run_steps(c, final_mode ? K - 1 : K, s);
-    if (st != SFSEG_OK) return st;
-    if (final_mode) {
-        CUDA_OR(c, launch_set_ptrs(c->d_out, d_x, c->nv, s));
-        CUDA_OR(c, launch_step(c, K - 1, true, true, s));
-        c->launches += 1;   // set_ptrs
+    if (c->path == SFSEG_PATH_FUSED) {
+        if (final_mode) {
+            CUDA_OR(c, launch_set_ptrs(c->d_out, d_x, c->nv, s));
+            c->launches += 1;
+        }
+        st = run_fused(c, K, final_mode, s);
+        if (st != SFSEG_OK) return st;
+    } else {
+        st = run_steps(c, final_mode ? K - 1 : K, s);
+        if (st != SFSEG_OK) return st;
+        if (final_mode) {
+            CUDA_OR(c, launch_set_ptrs(c->d_out, d_x, c->nv, s));
+            CUDA_OR(c, launch_step(c, K - 1, true, true, s));
+            c->launches += 1;   // set_ptrs
+        }
     }
     for (int v = 0; v < c->nv; ++v) {
         FinishParams F{};
@@ -1261,7 +1573,9 @@ sfseg_status sfseg_get_warnings(sfseg_ctx* c, int32_t* flags) {
 sfseg_status sfseg_debug_inject_timeout(sfseg_ctx* c, int32_t n_steps) {
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (n_steps < 0) return fail(c, SFSEG_EINVAL, "n_steps must be >= 0");
-    if (!c->fast) return fail(c, SFSEG_EUNSUPPORTED, "timeouts exist only in the specialised step kernel");
+    if (!c->fast && c->path != SFSEG_PATH_FUSED)
+        return fail(c, SFSEG_EUNSUPPORTED,
+                    "timeouts exist only in the specialised step kernel and the fused launch");
     c->inject_steps = n_steps;
     return SFSEG_OK;
 }
@@ -1291,6 +1605,14 @@ const char* sfseg_status_string(sfseg_status st) {
 }
 
 int64_t sfseg_launch_count(const sfseg_ctx* c) { return c ? c->launches : 0; }
+
+sfseg_status sfseg_get_path(const sfseg_ctx* c, int32_t* path, int32_t* fused_ctas, double* us_per_step) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (path) *path = c->path;
+    if (fused_ctas) *fused_ctas = c->path == SFSEG_PATH_FUSED ? c->fused_ctas : 0;
+    if (us_per_step) memcpy(us_per_step, c->tuned_us, sizeof c->tuned_us);
+    return SFSEG_OK;
+}
 
 int32_t sfseg_plan_segments(int32_t n_videos, const int32_t* dims, int32_t n_sms,
                             int32_t* segments, int32_t seg_cap, int32_t* cta_begin,

@@ -262,9 +262,34 @@ __device__ __forceinline__ void block_sum_lane0(double (&acc)[kRed], double* sh)
     __syncthreads();
 }
 
+// Power-of-two helpers for the gain by the FP64 exponent bits (integer
+// operations only: FP64 division, square roots and transcendental functions
+// are slow on this GPU and sit on the critical path of every power step).
+// 1 / v for v = 2^e in the normal range (exact).
+__device__ __forceinline__ double pow2_recip(double v) {
+    const long long ex = (__double_as_longlong(v) >> 52) & 0x7ff;
+    return __longlong_as_double((2046ll - ex) << 52);
+}
+// e with |log2(v) - e| <= 1/2 for a finite v > 0: the binary exponent, one
+// more when the mantissa exceeds sqrt(2).
+__device__ __forceinline__ int pow2_exponent_near(double v) {
+    const long long b = __double_as_longlong(v);
+    int e = (int)((b >> 52) & 0x7ff) - 1023;
+    if ((b & 0xfffffffffffffll) > 0x6a09e667f3bccll) e += 1;
+    return e;
+}
+// 2^e, e clamped to the normal range
+__device__ __forceinline__ double pow2(int e) {
+    e = e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+
 // The step's scalar update (Eq. 3 Rayleigh quotient, residual, Eq. 8 norm),
 // from the FP64 sums S = (z.z, xh.z, xh.xh, |z - shift xh|^2) of video v.
-// Runs in one thread.
+// Runs in one thread.  One FP64 division, one reciprocal square root and one
+// square root; the gain (a power of two, so that the stored z has RMS ~ 1 in
+// every storage type) is chosen from exponent bits.  The gain only rescales
+// the stored iterate by an exact power of two, which the next scale undoes.
 __device__ inline void finish_step(VState* st, double* trace_row, const double (&S)[kRed],
                                    long long n_vox, const Record* rec = nullptr) {
     const double zz = S[0], xz = S[1], xx = S[2], dd = S[3];
@@ -279,13 +304,16 @@ __device__ inline void finish_step(VState* st, double* trace_row, const double (
         st->done = 1;
         return;
     }
-    const double ny = sqrt(zz) / gain;          // ||M x_hat||, x_hat of unit norm
-    const double rz = xz / xx;                   // Rayleigh quotient of z = gain * M x_hat
-    const double r = rz / gain;
+    const double ig = pow2_recip(gain);
+    const double rxx = 1.0 / xx;
+    const double rsz = rsqrt(zz);                // 1 / ||z||
+    const double ny = zz * rsz * ig;             // ||M x_hat||, x_hat of unit norm
+    const double rz = xz * rxx;                  // Rayleigh quotient of z = gain * M x_hat
+    const double r = rz * ig;
     // ||z - rz xh||^2 = ||z - sig xh||^2 - (rz - sig)^2 xh.xh  (exact identity)
     double e = dd - (rz - sig) * (rz - sig) * xx;
     if (e < 0.0) e = 0.0;
-    const double rho = sqrt(e / xx) / gain;
+    const double rho = sqrt(e * rxx) * ig;
     if (trace_row) {
         trace_row[0] = r;
         trace_row[1] = rho;
@@ -295,11 +323,12 @@ __device__ inline void finish_step(VState* st, double* trace_row, const double (
     if (rec && rec->scale) {
         rec->gain[st->iter] = gain;
         rec->ny[st->iter] = ny;
-        rec->scale[st->iter + 1] = 1.0 / sqrt(zz);
+        rec->scale[st->iter + 1] = rsz;
     }
-    st->scale = 1.0 / sqrt(zz);
-    const double target = sqrt((double)n_vox) * sqrt(xx) / ny;
-    st->gain = exp2(rint(log2(target)));
+    st->scale = rsz;
+    // next gain ~ sqrt(n xh.xh) / ny; its square is n xx (rsz gain)^2
+    const double q = rsz * gain;
+    st->gain = pow2(pow2_exponent_near((double)n_vox * xx * q * q) >> 1);
     st->shift = st->gain * r;
     st->iter += 1;
     if (st->tol > 0.0 && rho < st->tol * fabs(r)) st->done = 1;

@@ -159,4 +159,35 @@ void fast_box(int ry, int* box_w, int* box_h, int* x_pad);   // TMA box of one s
 cudaError_t setup_step_fast(int rt, int ry, int rx, int storage);
 cudaError_t launch_step_fast(int storage, const StepParams& P, int n_ctas, cudaStream_t s);
 
+// ------------------------------------------------------- fused multi-step
+// All K power steps of a context in one cooperative launch (step_fused.cu):
+// per step a phase of y/x passes into an FP32 scratch, a grid barrier, a
+// phase of t-pass + combine + reductions + finalize, a grid barrier.
+struct FusedParams {
+    StepParams S;               // taps, alpha, geo, sp, f, state, trace, final_out; items /
+                                // cta_begin / item_begin / vseg / partials / counters describe
+                                // the phase-2 runs (item t0..t1 = unit range of its video)
+    const void* buf0;           // stored iterate of even steps (x_a)
+    void* buf1;                 // stored iterate of odd steps (x_b)
+    float* pvol;                // scratch: 3 FP32 volumes (packed pitched layout), channel c at + c * total
+    long long total;            // packed elements per volume
+    const int* unit1_begin;     // [n_videos + 1]: phase-1 units (frame x 32x16 tile) of video v
+    int n_units1;
+    int n_videos;
+    int n_steps;                // K
+    int final_mode;             // the last step writes the caller's FP32 buffers (S.final_out)
+    unsigned* bar;              // [3]: barrier count, generation, abort flag (zero before the launch)
+};
+
+// rows of one phase-2 unit of the fused kernel for a video of width w
+__host__ __device__ inline int fused_rows2(int w) {
+    const int r = 1024 / (w > 0 ? w : 1);
+    return r < 1 ? 1 : r;
+}
+
+size_t fused_smem_bytes(int ry, int rx);
+void fused_tile(int* tx, int* ty, int* threads);
+cudaError_t setup_step_fused(int storage, int ry, int rx, int* max_ctas);
+cudaError_t launch_step_fused(int storage, const FusedParams& F, int n_ctas, cudaStream_t s);
+
 }  // namespace sfseg

@@ -46,8 +46,8 @@ def test_default_params_and_status_strings(lib):
 
 @pytest.mark.parametrize("field,value", [("rx", -1), ("ry", 17), ("rt", 9), ("sigma_t", 0.0),
                                          ("alpha", -1.0), ("p", float("nan")), ("storage", 3),
-                                         ("nf", 0), ("w", -5), ("nchan", 0), ("flags", 16),
-                                         ("flags", -1)])
+                                         ("nf", 0), ("w", -5), ("nchan", 0), ("flags", 64),
+                                         ("flags", -1), ("flags", 16 | 8), ("flags", 16 | 32)])
 def test_create_rejects_bad_params(lib, field, value):
     """Validation happens on the host before any device call."""
     p = sf.sfseg_default_params(4, 8, 8)
@@ -58,11 +58,23 @@ def test_create_rejects_bad_params(lib, field, value):
     assert sf.sfseg_last_error(None)
 
 
+@pytest.mark.parametrize("flags,nchan", [(16 | 4, 1), (32 | 4, 1), (16, 2)])
+def test_create_rejects_unsupported_paths(lib, flags, nchan):
+    """The fused launch runs one channel and is not recorded for the adjoint;
+    the autotuner does not choose for recorded contexts (host-side checks)."""
+    p = sf.sfseg_default_params(4, 8, 8)
+    p.flags, p.nchan = flags, nchan
+    with pytest.raises(sf.SFSegError) as ei:
+        sf.sfseg_create(p)
+    assert ei.value.status == sf.SFSEG_EUNSUPPORTED
+
+
 def test_null_context_calls(lib):
     assert lib.sfseg_power_iterate(None, None, None, None, 1, 0.0, None, None) == sf.SFSEG_EINVAL
     assert lib.sfseg_get_trace(None, 0, None, None, None, 0) == -1
     lib.sfseg_destroy(None)
     assert lib.sfseg_launch_count(None) == 0
+    assert lib.sfseg_get_path(None, None, None, None) == sf.SFSEG_EINVAL
 
 
 @pytest.mark.parametrize("nchan,radii", [(5, (2, 5, 5)), (8, (1, 1, 1)), (4, (8, 16, 16)),
