@@ -176,7 +176,7 @@ struct FusedParams {
     int n_videos;
     int n_steps;                // K
     int final_mode;             // the last step writes the caller's FP32 buffers (S.final_out)
-    unsigned* bar;              // [3]: barrier count, generation, abort flag (zero before the launch)
+    unsigned* bar;              // [3]: barrier arrival count, (unused), abort flag (zero before the launch)
 };
 
 // rows of one phase-2 unit of the fused kernel for a video of width w

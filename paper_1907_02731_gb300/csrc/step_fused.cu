@@ -45,28 +45,33 @@ __device__ __forceinline__ unsigned long long fu_ns() {
     return t;
 }
 
-// Grid-wide barrier of the cooperative launch (sense by generation).  The
-// last CTA to arrive resets the count and advances the generation.  Returns
-// false when the wait gave up (time limit or the abort flag); `skip_arrive`
-// (fault injection for tests) makes the CTA wait without arriving, so the
-// barrier can never complete.
-__device__ bool grid_barrier(unsigned* bar, unsigned n_ctas, unsigned& gen, bool skip_arrive) {
+// Grid-wide barrier of the cooperative launch: a monotonic arrival count
+// (zeroed before the launch).  Barrier b (0, 1, ...) completes when the count
+// reaches (b + 1) G; arrival is a release add, the wait an acquire load, so a
+// CTA sees every write the others made before arriving.  Returns false when
+// the wait gave up (time limit, or the grid-wide abort flag raised by a CTA
+// that gave up); `skip_arrive` (fault injection for tests) makes the CTA wait
+// without arriving, so the barrier can never complete.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ bool grid_barrier(unsigned* bar, unsigned n_ctas, unsigned& nb, bool skip_arrive) {
     __shared__ int s_ok;
-    __syncthreads();
+    __syncthreads();   // the block's writes precede thread 0's release
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = bar + 1;
-        volatile int* abort = reinterpret_cast<volatile int*>(bar + 2);
+        const volatile int* abort = reinterpret_cast<volatile int*>(bar + 2);
+        const unsigned target = (nb + 1) * n_ctas;
         int ok = 1;
-        __threadfence();   // this CTA's writes before its arrival
-        const unsigned g0 = gen;
-        if (!skip_arrive && atomicAdd(bar, 1u) == n_ctas - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (!skip_arrive) red_release_add(bar, 1u);
+        if (ld_acquire(bar) < target) {
             const unsigned long long t0 = fu_ns();
             unsigned i = 0;
-            while (*vgen == g0) {
+            while (ld_acquire(bar) < target) {
                 if (*abort) { ok = 0; break; }
                 if ((++i & 31u) == 0u && fu_ns() - t0 > kFusedWaitNs) {
                     atomicExch(reinterpret_cast<int*>(bar + 2), 1);
@@ -75,8 +80,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned n_ctas, unsigned& gen, bool
                 }
             }
         }
-        __threadfence();   // the other CTAs' writes before this CTA reads
-        gen = g0 + 1;
+        nb += 1;
         s_ok = ok;
     }
     __syncthreads();
@@ -139,7 +143,7 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
     float* inb = sm;              // [3][TYH][TXH] point-wise products with halo
     float* yp = inb + 3 * IN;     // [3][FU_TY][TXH] after the y-pass
     const unsigned G = gridDim.x;
-    unsigned gen = 0;
+    unsigned nb = 0;   // barriers passed
     __shared__ int s_all_done;
     __shared__ float s_sg, s_scale, s_shift;
     __shared__ int s_skip;
@@ -151,12 +155,10 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
         const bool final_step = F.final_mode && k == F.n_steps - 1;
 
         // ------------------------------------------------ phase 1: y, x passes
-        // (the done flags read here may lag one finalize behind: a video that
-        // just finished is filtered once more into the scratch, which nothing
-        // reads; phase 2 reads the settled flags)
+        // (videos that are done are filtered too -- the scratch of a finished
+        // video is never read -- so that phase 1 waits on no scalar)
         for (int u = blockIdx.x; u < F.n_units1; u += G) {
             const int v = unit_video(F.unit1_begin, F.n_videos, u);
-            if (__ldcg(&P.state[v].done)) continue;
             const VideoGeom g = P.geo[v];
             const int ntx = (g.w + FU_TX - 1) / FU_TX, nty = (g.h + FU_TY - 1) / FU_TY;
             const int local = u - F.unit1_begin[v];
@@ -270,14 +272,23 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
             }
             __syncthreads();   // inb / yp are reused by the next unit
         }
-        if (!grid_barrier(F.bar, G, gen, P.inject_timeout && blockIdx.x == 0 && k == 0)) goto timed_out;
+        if (!grid_barrier(F.bar, G, nb, P.inject_timeout && blockIdx.x == 0 && k == 0)) goto timed_out;
 
         // every CTA reads the same settled scalars (the finalize of the step
-        // before ran ahead of its CTA's arrival at this barrier)
+        // before ran ahead of its CTA's arrival at this barrier); with one
+        // video they are kept for phase 2 as well
         if (threadIdx.x == 0) {
             int all = 1;
             for (int v = 0; v < F.n_videos; ++v) all &= __ldcg(&P.state[v].done);
             s_all_done = all;
+            if (F.n_videos == 1) {
+                const VState* st = P.state;
+                const double sc = __ldcg(&st->scale);
+                s_skip = all;
+                s_scale = (float)sc;
+                s_sg = (float)(sc * __ldcg(&st->gain));
+                s_shift = (float)__ldcg(&st->shift);
+            }
         }
         __syncthreads();
         if (s_all_done) break;
@@ -289,7 +300,7 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
                 const WorkItem item = P.items[it];
                 const int v = item.video;
                 __syncthreads();   // s_* of the previous item are no longer read
-                if (threadIdx.x == 0) {
+                if (threadIdx.x == 0 && F.n_videos > 1) {
                     const VState* st = P.state + v;
                     s_skip = __ldcg(&st->done);
                     const double sc = __ldcg(&st->scale);
@@ -372,7 +383,7 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
                     for (int c = 0; c < kRed; ++c) P.partials[(long long)it * kRed + c] = acc[c];
             }
         }
-        if (!grid_barrier(F.bar, G, gen, false)) goto timed_out;
+        if (!grid_barrier(F.bar, G, nb, false)) goto timed_out;
         // finalize: CTA v mod G updates video v; the next phase 1 needs no
         // scalars, and the next phase 2 starts after the next barrier
         for (int v = blockIdx.x; v < F.n_videos; v += G) fused_finalize(P, v, reinterpret_cast<double*>(sm));
