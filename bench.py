@@ -240,7 +240,7 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
-def workload_config(wl, storage, prob=None):
+def workload_config(wl, storage, prob=None, split=None, world=1):
     cfg = {"workload": wl.name, "frames": wl.nf, "h": wl.h, "w": wl.w,
            "kernel": f"{2 * wl.rx + 1}x{2 * wl.ry + 1}x{2 * wl.rt + 1}",
            "sigma_xy": wl.sigma_xy, "sigma_t": wl.sigma_t, "alpha": wl.alpha, "p": wl.p,
@@ -252,6 +252,9 @@ def workload_config(wl, storage, prob=None):
                     % (prob.n * 4 / 1e6)})
     if wl.name.startswith("grad"):
         cfg["step"] = "recorded forward + adjoint (checkpoints every 8)"
+    if split == "t":
+        cfg["split"] = ("one video split along t over %d ranks: per step an all-reduce of 4 FP64 "
+                        "sums and %d halo frames to each neighbour" % (world, wl.rt))
     return cfg
 
 
@@ -430,6 +433,56 @@ class Batch:
                 "videos": len(self.xs), "voxels": self.n}
 
 
+class SplitVideo:
+    """One video split along t over the ranks (strong scaling): rank r owns a
+    contiguous slab of frames plus rt halo frames per side; per power step the
+    ranks all-reduce four FP64 sums (NCCL) and exchange rt frames with each
+    neighbour (NCCL send/recv).  One bench step = one whole call: features of
+    the slab loaded, 50 steps, the own frames of the unit-norm x^K.  Every
+    rank draws the same seeded video; `n` is this rank's own voxels, so the
+    sum over ranks is the whole video."""
+
+    def __init__(self, wl, storage, rank, dev, sf, inputs, world=1):
+        import torch
+        from paper_1907_02731_gb300 import slab
+        self.wl, self.K, self.world, self.rank = wl, wl.iters, world, rank
+        s_np, f_np = inputs.workload_features(wl.name, rank_video_index(0))
+        if wl.nchan != 1:
+            raise SystemExit("--split t: one pairwise channel")
+        a, b = slab.split_frames(wl.nf, world, wl.rt)[rank]
+        lo, hi = slab.slab_frames(wl.nf, a, b, wl.rt)
+        self.n = (b - a) * wl.h * wl.w
+        self.s = torch.from_numpy(np.ascontiguousarray(s_np[lo:hi])).to(dev)
+        self.x0 = self.s
+        self.eng = slab.LibSlab((wl.nf, wl.h, wl.w), a, b, radii=(wl.rt, wl.ry, wl.rx),
+                                sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
+                                storage=storage)
+        self.comm = slab.TorchComm() if world > 1 else slab.LocalComm()
+        self.proto = slab.SlabProtocol(self.eng, self.comm, rank, world)
+        self.f_host = torch.from_numpy(np.ascontiguousarray(s_np[lo:hi])).pin_memory()
+        self.f_dev = torch.empty_like(self.s)
+        self.out_host = torch.empty((b - a, wl.h, wl.w), dtype=torch.float32).pin_memory()
+        self.h2d = int(self.f_host.numel() * 4)
+        self.d2h = int(self.out_host.numel() * 4)
+        self.x = None
+
+    def step(self, iters):
+        self.eng.load_features(self.s, self.s)
+        self.x = self.proto.run(self.x0, iters)
+
+    def e2e_step(self):
+        self.f_dev.copy_(self.f_host, non_blocking=True)
+        self.eng.load_features(self.f_dev, self.f_dev)
+        x = self.proto.run(self.f_dev, self.K)
+        self.out_host.copy_(x, non_blocking=True)
+
+    def check(self):
+        import torch
+        tr = self.eng.trace()
+        return {"own_x_sq_norm": float(torch.sum(self.x.double() ** 2)), "ranks": self.world,
+                "rayleigh_last": float(tr["rayleigh"][-1])}
+
+
 class Grad:
     """Differentiable form: 854x480x48, 40 recorded power steps, then the
     adjoint of L = sum(target * x^K) w.r.t. sp, f and x0 (checkpoints every 8
@@ -488,7 +541,11 @@ def run_ours(args, wl):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     kind = {"batch_24": Batch, "grad_48x480x854": Grad}.get(wl.name, SingleVideo)
-    prob = kind(wl, args.storage, rank, dev, sf, inputs)
+    if args.split == "t":
+        kind = SplitVideo
+        prob = kind(wl, args.storage, rank, dev, sf, inputs, world)
+    else:
+        prob = kind(wl, args.storage, rank, dev, sf, inputs)
     K = prob.K
 
     def barrier():
@@ -571,9 +628,9 @@ def run_ours(args, wl):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.storage, "data": "synthetic",
-            "config": workload_config(wl, args.storage, prob),
+            "higher_is_better": True, "scaling": "strong" if kind is SplitVideo else "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": workload_config(wl, args.storage, prob, split=args.split, world=world),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": DRAM_TRAFFIC_PER_LAUNCH.get((wl.name, args.storage)),
@@ -823,6 +880,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="video_72x480x854")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--split", default=None, choices=["t"],
+                    help="one video split along t over the ranks (strong scaling) instead of one "
+                         "video per rank")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--accuracy", action="store_true",
                     help="report x^K errors of FP32/BF16/FP16 storage against the FP64 oracle")

@@ -276,6 +276,88 @@ sfseg_status sfseg_power_iterate_noalloc(const sfseg_params* prm, const float* d
                                          const float* d_f, float* d_x, int32_t n_iters,
                                          double* d_trace, void* stream);
 
+/* ---- One video split along t over several GPUs (one process per GPU).
+ * The operator is local (Eq. 7: a separable Gaussian of radii (rt, ry, rx),
+ * and "highly parallelizable", Sec. 4), so a video of nf frames cuts into
+ * contiguous slabs of frames, one per rank.  A rank owning frames [a, b)
+ * keeps the slab [a - rt, b + rt) clipped to the video: its own frames plus
+ * up to rt halo frames on each side.  Per power step each rank computes M x
+ * on its own frames; the step's four FP64 sums (z.z, x.z, x.x, |z - s x|^2,
+ * the inputs of Eq. 3 and Eq. 8) are summed over all ranks (an all-reduce the
+ * caller runs, e.g. NCCL) and applied on every rank, so every rank holds the
+ * same norm, Rayleigh quotient and trace; then neighbours exchange rt frames
+ * of the new stored iterate (the caller moves the bytes, e.g. NCCL send/recv
+ * or a peer copy).  One step on R ranks:
+ *     sfseg_slab_step(ctx, d_part)          partial sums of the own frames
+ *     all-reduce (sum) d_part -> d_sum      4 doubles, over the ranks
+ *     sfseg_slab_finish_step(ctx, d_sum)    norm, Rayleigh quotient, residual
+ *     halo exchange                          pack (dir 0) own edge frames into
+ *                                            send buffers, the caller sends them,
+ *                                            unpack (dir 1) received frames
+ * The start: sfseg_load_features on the slab's frames, sfseg_slab_start
+ * (partial sum of x0^2 of the own frames), all-reduce, sfseg_slab_set_norm.
+ * The end: sfseg_slab_output writes the own frames of the unit-norm x^K.
+ * Fixed step count (no early stop), one video per context, the per-step
+ * kernels.  All device pointers; all calls are stream-ordered, none
+ * synchronises.  With one rank (a = 0, b = nf) this is sfseg_power_iterate
+ * split into its steps. */
+
+/* prm: the slab's shape (nf = its frame count including the halo frames) and
+ * the video's parameters; own frames [own_lo, own_hi) of the slab; the halo
+ * on either side has at most rt frames, and a slab with a neighbour owns at
+ * least rt frames (a halo then comes from one neighbour); video_voxels: the
+ * voxel count of the whole video (it sets the storage gain, the same on
+ * every rank).  Errors: EINVAL, EUNSUPPORTED (SFSEG_FUSED, SFSEG_AUTOTUNE,
+ * SFSEG_RECORD), ENOMEM, ECUDA. */
+sfseg_status sfseg_create_slab(const sfseg_params* prm, int32_t own_lo, int32_t own_hi,
+                               int64_t video_voxels, sfseg_ctx** out);
+
+/* Store x0 (d_x0: the slab's [nf][h][w] FP32 frames, halo frames included)
+ * and write the sum of x0^2 over the own frames to d_part[0] (device double).
+ * n_iters: the number of steps that will follow (trace capacity; may
+ * synchronise the device to grow it).  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_start(sfseg_ctx* ctx, const float* d_x0, int32_t n_iters, double* d_part,
+                              void* stream);
+
+/* Start the iteration from d_sumsq[0] = the sum of x0^2 over the whole video
+ * (device double, the all-reduced sfseg_slab_start partials).  A zero or
+ * non-finite sum sets SFSEG_EZERONORM / SFSEG_ENONFINITE on the device
+ * (sfseg_sync_status).  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_set_norm(sfseg_ctx* ctx, const double* d_sumsq, void* stream);
+
+/* One power step on the own frames: y = M x (Eq. 7) stored for the next step,
+ * and the four FP64 sums of the own frames written to d_part[0..3] (device):
+ * z.z, x.z, x.x and |z - s x|^2 (z the stored step output, x the scaled
+ * input, s the previous Rayleigh quotient times the gain).  d_x_final
+ * (nullable): this is the last step, and its output goes in FP32 to d_x_final
+ * (the own frames, [own_hi - own_lo][h][w], device) instead of the storage
+ * type; pass the same buffer to sfseg_slab_output.  At most n_iters steps per
+ * sfseg_slab_start.  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_step(sfseg_ctx* ctx, double* d_part, float* d_x_final, void* stream);
+
+/* Apply the step's sums over all ranks (d_sums[0..3], device): Rayleigh
+ * quotient, residual and norm into the trace, the next scale and gain
+ * (Eq. 3, Eq. 8).  Every rank passes the same sums, so every rank holds the
+ * same scalars.  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_finish_step(sfseg_ctx* ctx, const double* d_sums, void* stream);
+
+/* Halo exchange of the stored iterate the next step reads, in the storage
+ * type and the library's row layout: frames of [h][pitch] elements, pitch = w
+ * rounded up to 8 (pad columns zero).  side 0 = the low-frame end, 1 = the
+ * high end; dir 0 packs the rt own frames at that end into d_buf (for the
+ * neighbour on that side), dir 1 unpacks d_buf into the halo frames at that
+ * end (received from that neighbour).  sfseg_slab_halo_bytes gives the byte
+ * count of (side, dir), or -1 for a bad argument; 0 means nothing to move.
+ * Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_halo(sfseg_ctx* ctx, int32_t side, int32_t dir, void* d_buf, void* stream);
+int64_t sfseg_slab_halo_bytes(const sfseg_ctx* ctx, int32_t side, int32_t dir);
+
+/* The own frames of the unit-norm x^K (FP32, [own_hi - own_lo][h][w],
+ * device) after the last finish_step: scaled in place when d_x is the buffer
+ * the last sfseg_slab_step wrote (FP32 throughout), else read from the stored
+ * iterate (rounded to the storage type).  Errors: EINVAL, ESTATE, ECUDA. */
+sfseg_status sfseg_slab_output(sfseg_ctx* ctx, float* d_x, void* stream);
+
 /* Message of the last failure on ctx (ctx may be NULL: last create failure). */
 const char* sfseg_last_error(const sfseg_ctx* ctx);
 

@@ -36,7 +36,9 @@ EXPORTS = (
     "sfseg_adjoint", "sfseg_sync_status", "sfseg_last_error", "sfseg_status_string",
     "sfseg_launch_count", "sfseg_power_iterate_noalloc", "sfseg_plan_segments",
     "sfseg_default_binarize", "sfseg_power_iterate_binarized", "sfseg_debug_inject_timeout",
-    "sfseg_get_warnings", "sfseg_get_path",
+    "sfseg_get_warnings", "sfseg_get_path", "sfseg_create_slab", "sfseg_slab_start",
+    "sfseg_slab_set_norm", "sfseg_slab_step", "sfseg_slab_finish_step", "sfseg_slab_halo",
+    "sfseg_slab_halo_bytes", "sfseg_slab_output",
 )
 SFSEG_WARN_NEGATIVE_M = 1
 
@@ -104,6 +106,14 @@ def load_library(path: str = LIB_PATH):
         "sfseg_debug_inject_timeout": (_i32, [_vp, _i32]),
         "sfseg_get_warnings": (_i32, [_vp, ctypes.POINTER(_i32)]),
         "sfseg_get_path": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
+        "sfseg_create_slab": (_i32, [P, _i32, _i32, ctypes.c_int64, ctypes.POINTER(_vp)]),
+        "sfseg_slab_start": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+        "sfseg_slab_set_norm": (_i32, [_vp, _vp, _vp]),
+        "sfseg_slab_step": (_i32, [_vp, _vp, _vp, _vp]),
+        "sfseg_slab_finish_step": (_i32, [_vp, _vp, _vp]),
+        "sfseg_slab_halo": (_i32, [_vp, _i32, _i32, _vp, _vp]),
+        "sfseg_slab_halo_bytes": (ctypes.c_int64, [_vp, _i32, _i32]),
+        "sfseg_slab_output": (_i32, [_vp, _vp, _vp]),
         "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
                                                  ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
@@ -270,6 +280,44 @@ def sfseg_get_path(ctx: int):
     path, ctas, us = _i32(), _i32(), (_dbl * 3)()
     _check(load_library().sfseg_get_path(ctx, ctypes.byref(path), ctypes.byref(ctas), us), ctx)
     return path.value, ctas.value, list(us)
+
+
+def sfseg_create_slab(params: sfseg_params, own_lo: int, own_hi: int, video_voxels: int) -> int:
+    out = _vp()
+    _check(load_library().sfseg_create_slab(ctypes.byref(params), own_lo, own_hi, video_voxels,
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def sfseg_slab_start(ctx: int, d_x0: int, n_iters: int, d_part: int, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_start(ctx, d_x0, n_iters, d_part, stream), ctx)
+
+
+def sfseg_slab_set_norm(ctx: int, d_sumsq: int, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_set_norm(ctx, d_sumsq, stream), ctx)
+
+
+def sfseg_slab_step(ctx: int, d_part: int, d_x_final=None, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_step(ctx, d_part, d_x_final, stream), ctx)
+
+
+def sfseg_slab_finish_step(ctx: int, d_sums: int, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_finish_step(ctx, d_sums, stream), ctx)
+
+
+def sfseg_slab_halo(ctx: int, side: int, direction: int, d_buf: int, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_halo(ctx, side, direction, d_buf, stream), ctx)
+
+
+def sfseg_slab_halo_bytes(ctx: int, side: int, direction: int) -> int:
+    n = load_library().sfseg_slab_halo_bytes(ctx, side, direction)
+    if n < 0:
+        _check(SFSEG_EINVAL, ctx)
+    return n
+
+
+def sfseg_slab_output(ctx: int, d_x: int, stream: int = 0) -> None:
+    _check(load_library().sfseg_slab_output(ctx, d_x, stream), ctx)
 
 
 # --------------------------------------------------- torch convenience wrapper

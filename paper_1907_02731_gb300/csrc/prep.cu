@@ -118,7 +118,19 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
     TS* Xo = (TS*)P.x_out + g.off;
     float part = 0.f;
     int bad = 0;
-    if (aligned8(P.x) && pair_batch_ok(g)) {
+    if (P.ext_sum) {   // slab: store every frame, count only [norm_t0, norm_t1) in the norm
+        const long long hw = (long long)g.h * g.w;
+        for_each_voxel(g, [&](long long i, long long o) {
+            const TS xs = from_f<TS>(P.x[i]);
+            const float xv = to_f(xs);
+            const long long t = i / hw;
+            Xo[o] = xs;
+            if (t >= P.norm_t0 && t < P.norm_t1) {
+                bad |= !isfinite(xv);
+                part = fmaf(xv, xv, part);
+            }
+        });
+    } else if (aligned8(P.x) && pair_batch_ok(g)) {
         constexpr int U = 4;
         for_each_pair_batch<U>(g, [&](const long long (&i)[U], const long long (&o)[U], const bool (&ok)[U]) {
             float2 xv[U];
@@ -164,6 +176,10 @@ __global__ void __launch_bounds__(256) prep_x_kernel(const __grid_constant__ Pre
     const double xx = block_sum_partials(P.partials, (int)gridDim.x);
     if (threadIdx.x != 0) return;
     *P.counter = 0u;
+    if (P.ext_sum) {
+        *P.ext_sum = xx;   // NaN when a stored value was not finite
+        return;
+    }
     VState st;
     st.tol = P.tol;
     st.iter = 0;
@@ -277,6 +293,42 @@ cudaError_t launch_finish(int storage, const FinishParams& P, cudaStream_t s) {
         case 2: finish_kernel<__half><<<b, 256, 0, s>>>(P); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaPeekAtLastError();
+}
+
+// Slab scalars (one thread).  mode 0: the start of the iteration from the
+// global sum of x0^2, as the tail of prep_x; mode 1: the step's global sums
+// through the same finish_step as every other path.
+__global__ void slab_state_kernel(VState* st, const double* sums, int mode, double gain0,
+                                  long long n_video, double* trace, int trace_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (mode == 0) {
+        const double xx = sums[0];
+        VState v;
+        v.tol = 0.0;
+        v.iter = 0;
+        v.final_iter = -1;
+        v.shift = 0.0;
+        v.status = 0;
+        v.done = 0;
+        v.gain = gain0;
+        v.in_norm = (isfinite(xx) && xx > 0.0) ? sqrt(xx) : 1.0;
+        if (!isfinite(xx)) { v.status = 5; v.done = 1; v.scale = 0.0; }
+        else if (!(xx > 0.0)) { v.status = 4; v.done = 1; v.scale = 0.0; }
+        else v.scale = 1.0 / sqrt(xx);
+        *st = v;
+        return;
+    }
+    if (st->done) return;
+    double S[kRed];
+    for (int c = 0; c < kRed; ++c) S[c] = sums[c];
+    const int k = st->iter;
+    finish_step(st, k < trace_cap ? trace + 3ll * k : nullptr, S, n_video, nullptr);
+}
+
+cudaError_t launch_slab_state(VState* st, const double* sums, int mode, double gain0, long long n_video,
+                              double* trace, int trace_cap, cudaStream_t s) {
+    slab_state_kernel<<<1, 32, 0, s>>>(st, sums, mode, gain0, n_video, trace, trace_cap);
     return cudaPeekAtLastError();
 }
 

@@ -103,6 +103,14 @@ struct sfseg_ctx {
     double* d_fpartials = nullptr;
     unsigned* d_fbar = nullptr; // [3]
     float* d_pvol = nullptr;    // 3 FP32 volumes
+    // slab of a video split along t (sfseg_create_slab): own output frames
+    // [own_lo, own_hi) of the context's volume, the voxel count of the whole
+    // video (the gain rule), steps completed (parity of the stored iterate)
+    bool slab = false;
+    int own_lo = 0, own_hi = 0;
+    long long video_voxels = 0;
+    int slab_k = 0;
+    float* slab_final = nullptr;   // the caller buffer the last slab step wrote in FP32
     std::vector<int> item_begin;
     // host-side
     float gt[2 * kMaxRt + 1], gy[2 * kMaxR + 1], gx[2 * kMaxR + 1];
@@ -213,13 +221,17 @@ static void host_taps(int r, double sigma, float* g, double* sum) {
 // item_begin) for the finalize.
 static void build_segments(const std::vector<VideoGeom>& geo, int sms, std::vector<WorkItem>* items,
                            std::vector<int>* item_begin, std::vector<int>* cta_begin,
-                           std::vector<int>* vseg) {
+                           std::vector<int>* vseg, int f_lo = 0, int f_hi = -1) {
+    // output frames [f_lo, f_hi) of every video (f_hi < 0: all frames); a
+    // slab of a video split along t computes its own frames only
     int tx, ty, nt;
     fast_tile(&tx, &ty, &nt);
     struct Tile { int v, x0, y0, nf; };
+    auto fr0 = [&](const VideoGeom& g) { return f_lo < g.nf ? f_lo : g.nf; };
+    auto fr1 = [&](const VideoGeom& g) { return f_hi < 0 || f_hi > g.nf ? g.nf : f_hi; };
     long long U = 0;
     for (const VideoGeom& g : geo)
-        U += (long long)g.nf * ((g.w + tx - 1) / tx) * ((g.h + ty - 1) / ty);
+        U += (long long)(fr1(g) - fr0(g)) * ((g.w + tx - 1) / tx) * ((g.h + ty - 1) / ty);
     long long n = U / 8;                      // at least ~8 output frames per CTA
     if (n > sms) n = sms;
     if (n < 1) n = 1;
@@ -232,15 +244,15 @@ static void build_segments(const std::vector<VideoGeom>& geo, int sms, std::vect
         const VideoGeom& g = geo[v];
         std::vector<Tile> tv;
         for (int y0 = 0; y0 < g.h; y0 += ty)
-            for (int x0 = 0; x0 < g.w; x0 += tx) tv.push_back({v, x0, y0, g.nf});
+            for (int x0 = 0; x0 < g.w; x0 += tx) tv.push_back({v, x0, y0, fr1(g) - fr0(g)});
         const size_t whole = tv.size() / (size_t)n * (size_t)n;
         for (size_t k = 0; k < whole; ++k) {
             WorkItem it{};
             it.video = v;
             it.x0 = tv[k].x0;
             it.y0 = tv[k].y0;
-            it.t0 = 0;
-            it.t1 = g.nf;
+            it.t0 = fr0(g);
+            it.t1 = fr1(g);
             per[k % n].push_back(it);
         }
         tiles.insert(tiles.end(), tv.begin() + whole, tv.end());
@@ -259,8 +271,8 @@ static void build_segments(const std::vector<VideoGeom>& geo, int sms, std::vect
             it.video = tiles[k].v;
             it.x0 = tiles[k].x0;
             it.y0 = tiles[k].y0;
-            it.t0 = (int)(t - pos);
-            it.t1 = (int)(e - pos);
+            it.t0 = fr0(geo[tiles[k].v]) + (int)(t - pos);
+            it.t1 = fr0(geo[tiles[k].v]) + (int)(e - pos);
             per[cur].push_back(it);
             t = e;
         }
@@ -420,7 +432,7 @@ static cudaError_t upload_fused_plan(sfseg_ctx* c, int G) {
 }
 
 static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* dims, bool batched,
-                                sfseg_ctx** out) {
+                                sfseg_ctx** out, int f_lo = 0, int f_hi = -1) {
     if (!out) return fail(nullptr, SFSEG_EINVAL, "out is NULL");
     *out = nullptr;
     sfseg_status st = validate(prm);
@@ -459,7 +471,7 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
             sms = 1;
-        build_segments(c->geo, sms, &items, &c->item_begin, &cta_begin, &vseg);
+        build_segments(c->geo, sms, &items, &c->item_begin, &cta_begin, &vseg, f_lo, f_hi);
         c->n_ctas = (int)cta_begin.size() - 1;
     }
     std::vector<WorkItem> gitems;
@@ -476,8 +488,8 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
                     it.video = v;
                     it.x0 = x0;
                     it.y0 = y0;
-                    it.t0 = 0;
-                    it.t1 = g.nf;
+                    it.t0 = f_lo;
+                    it.t1 = f_hi < 0 ? g.nf : f_hi;
                     gitems.push_back(it);
                 }
         }
@@ -496,8 +508,8 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
                     it.video = v;
                     it.x0 = x0;
                     it.y0 = y0;
-                    it.t0 = 0;
-                    it.t1 = g.nf;
+                    it.t0 = f_lo;
+                    it.t1 = f_hi < 0 ? g.nf : f_hi;
                     items.push_back(it);
                 }
         }
@@ -568,7 +580,7 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
         e = cudaMemcpy(c->d_gitem_begin, gitem_begin.data(), sizeof(int) * gitem_begin.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = setup_step_generic(prm->rt, prm->ry, prm->rx);
-    if (e == cudaSuccess && prm->nchan == 1 && !(prm->flags & SFSEG_RECORD)) {
+    if (e == cudaSuccess && prm->nchan == 1 && !(prm->flags & SFSEG_RECORD) && f_lo == 0 && f_hi < 0) {
         // fused path: its plan arrays hold the largest plan (one item per CTA
         // and video boundary); the scratch volumes are allocated on first use
         e = setup_step_fused(prm->storage, prm->ry, prm->rx, &c->fused_max);
@@ -685,8 +697,9 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
 }
 
 static cudaError_t launch_step(sfseg_ctx* c, int k, bool final_out, bool store, cudaStream_t s,
-                               bool record = false) {
+                               bool record = false, double* ext_sums = nullptr) {
     StepParams P = step_params(c, k, final_out, store, record);
+    P.ext_sums = ext_sums;
     if (c->inject_steps > 0) {
         P.inject_timeout = 1;
         c->inject_steps -= 1;
@@ -828,8 +841,11 @@ static sfseg_status load_features_impl(sfseg_ctx* c, const float* const* d_s, co
 }
 
 static sfseg_status prep_x(sfseg_ctx* c, int v, const float* d_x, bool raw, double tol, cudaStream_t s,
-                           double* rec_scale0 = nullptr) {
+                           double* rec_scale0 = nullptr, double* ext_sum = nullptr) {
     PrepXParams P{};
+    P.ext_sum = ext_sum;
+    P.norm_t0 = c->own_lo;
+    P.norm_t1 = c->own_hi;
     P.rec_scale0 = rec_scale0;
     P.x = d_x;
     P.x_out = c->xa;
@@ -1605,6 +1621,158 @@ const char* sfseg_status_string(sfseg_status st) {
 }
 
 int64_t sfseg_launch_count(const sfseg_ctx* c) { return c ? c->launches : 0; }
+
+// ------------------------------------------------ video split along t (slabs)
+sfseg_status sfseg_create_slab(const sfseg_params* prm, int32_t own_lo, int32_t own_hi,
+                               int64_t video_voxels, sfseg_ctx** out) {
+    if (!prm) return fail(nullptr, SFSEG_EINVAL, "params is NULL");
+    if (out) *out = nullptr;
+    sfseg_status st = validate(prm);
+    if (st != SFSEG_OK) return st;
+    if (prm->flags & (SFSEG_FUSED | SFSEG_AUTOTUNE | SFSEG_RECORD))
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "a slab runs the per-step kernels (no FUSED, AUTOTUNE, RECORD)");
+    if (own_lo < 0 || own_hi > prm->nf || own_lo >= own_hi)
+        return fail(nullptr, SFSEG_EINVAL, "own frames [%d, %d) outside the slab's %d frames", own_lo, own_hi,
+                    prm->nf);
+    if (own_lo > prm->rt || prm->nf - own_hi > prm->rt)
+        return fail(nullptr, SFSEG_EINVAL, "halo of %d and %d frames exceeds rt = %d", own_lo, prm->nf - own_hi,
+                    prm->rt);
+    if ((own_lo > 0 || own_hi < prm->nf) && own_hi - own_lo < prm->rt)
+        return fail(nullptr, SFSEG_EINVAL, "%d own frames: a slab with neighbours owns at least rt = %d",
+                    own_hi - own_lo, prm->rt);
+    const long long own_vox = (long long)(own_hi - own_lo) * prm->h * prm->w;
+    if (video_voxels < own_vox)
+        return fail(nullptr, SFSEG_EINVAL, "video_voxels %lld < the slab's own %lld", (long long)video_voxels,
+                    own_vox);
+    int32_t dims[3] = {prm->nf, prm->h, prm->w};
+    st = create_impl(prm, 1, dims, false, out, own_lo, own_hi);
+    if (st != SFSEG_OK) return st;
+    sfseg_ctx* c = *out;
+    c->slab = true;
+    c->own_lo = own_lo;
+    c->own_hi = own_hi;
+    c->video_voxels = video_voxels;
+    return SFSEG_OK;
+}
+
+static sfseg_status slab_ok(sfseg_ctx* c) {
+    if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
+    if (!c->slab) return fail(c, SFSEG_EINVAL, "not a slab context (sfseg_create_slab)");
+    if (!c->features) return fail(c, SFSEG_ESTATE, "no features loaded");
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_slab_start(sfseg_ctx* c, const float* d_x0, int32_t n_iters, double* d_part,
+                              void* stream) {
+    NvtxRange nvtx_range("sfseg_slab_start");
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_x0 || !d_part) return fail(c, SFSEG_EINVAL, "NULL pointer");
+    if (n_iters < 0) return fail(c, SFSEG_EINVAL, "n_iters must be >= 0");
+    if ((st = ensure_trace(c, n_iters > 0 ? n_iters : 1)) != SFSEG_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = prep_x(c, 0, d_x0, false, 0.0, s, nullptr, d_part);
+    if (st != SFSEG_OK) return st;
+    c->slab_k = 0;
+    c->recorded = false;
+    c->last_stream = s;
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_slab_set_norm(sfseg_ctx* c, const double* d_sumsq, void* stream) {
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_sumsq) return fail(c, SFSEG_EINVAL, "d_sumsq is NULL");
+    const double gain0 = std::exp2(std::rint(std::log2(std::sqrt((double)c->video_voxels) / c->gsum)));
+    CUDA_OR(c, launch_slab_state(c->d_state, d_sumsq, 0, gain0, c->video_voxels, c->d_trace, c->trace_cap,
+                                 (cudaStream_t)stream));
+    c->launches += 1;
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_slab_step(sfseg_ctx* c, double* d_part, float* d_x_final, void* stream) {
+    NvtxRange nvtx_range("sfseg_slab_step");
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_part) return fail(c, SFSEG_EINVAL, "d_part is NULL");
+    if (c->slab_k >= c->trace_cap) return fail(c, SFSEG_EINVAL, "more steps than sfseg_slab_start's n_iters");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_OR(c, cudaMemsetAsync(d_part, 0, sizeof(double) * kRed, s));   // a skipped (done) step sums to 0
+    c->slab_final = d_x_final;
+    if (d_x_final) {
+        // the kernel writes frame t of the slab at [(t * h + y) * w + x] of
+        // the pointer table's entry: offset it so the own frames land at 0
+        const VideoGeom& g = c->geo[0];
+        float* base = d_x_final - (long long)c->own_lo * g.h * g.w;
+        CUDA_OR(c, launch_set_ptrs(c->d_out, &base, 1, s));
+        c->launches += 1;
+    }
+    CUDA_OR(c, launch_step(c, c->slab_k, d_x_final != nullptr, true, s, false, d_part));
+    c->slab_k += 1;
+    c->last_stream = s;
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_slab_finish_step(sfseg_ctx* c, const double* d_sums, void* stream) {
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_sums) return fail(c, SFSEG_EINVAL, "d_sums is NULL");
+    CUDA_OR(c, launch_slab_state(c->d_state, d_sums, 1, 0.0, c->video_voxels, c->d_trace, c->trace_cap,
+                                 (cudaStream_t)stream));
+    c->launches += 1;
+    return SFSEG_OK;
+}
+
+int64_t sfseg_slab_halo_bytes(const sfseg_ctx* c, int32_t side, int32_t dir) {
+    if (!c || !c->slab || side < 0 || side > 1 || dir < 0 || dir > 1) return -1;
+    const VideoGeom& g = c->geo[0];
+    const long long frames = dir == 0 ? c->prm.rt : (side == 0 ? c->own_lo : g.nf - c->own_hi);
+    return frames * g.plane * (long long)c->elt;
+}
+
+sfseg_status sfseg_slab_halo(sfseg_ctx* c, int32_t side, int32_t dir, void* d_buf, void* stream) {
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_buf) return fail(c, SFSEG_EINVAL, "d_buf is NULL");
+    if (side < 0 || side > 1 || dir < 0 || dir > 1) return fail(c, SFSEG_EINVAL, "side and dir are 0 or 1");
+    const VideoGeom& g = c->geo[0];
+    const long long bytes = sfseg_slab_halo_bytes(c, side, dir);
+    if (bytes == 0) return SFSEG_OK;
+    // the stored iterate the next step reads
+    char* buf = (char*)((c->slab_k & 1) ? c->xb : c->xa) + (size_t)g.off * c->elt;
+    const long long pb = g.plane * (long long)c->elt;
+    const int rt = c->prm.rt;
+    char* frames = dir == 0 ? buf + (side == 0 ? c->own_lo : c->own_hi - rt) * pb
+                            : buf + (side == 0 ? 0 : c->own_hi) * pb;
+    if (dir == 0)
+        CUDA_OR(c, cudaMemcpyAsync(d_buf, frames, (size_t)bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    else
+        CUDA_OR(c, cudaMemcpyAsync(frames, d_buf, (size_t)bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return SFSEG_OK;
+}
+
+sfseg_status sfseg_slab_output(sfseg_ctx* c, float* d_x, void* stream) {
+    sfseg_status st = slab_ok(c);
+    if (st != SFSEG_OK) return st;
+    if (!d_x) return fail(c, SFSEG_EINVAL, "d_x is NULL");
+    FinishParams F{};
+    F.out = d_x;
+    F.buf0 = c->xa;
+    F.buf1 = c->xb;
+    F.g = c->geo[0];
+    F.g.nf = c->own_hi - c->own_lo;
+    F.g.off += (long long)c->own_lo * F.g.plane;
+    F.g.n = (long long)F.g.nf * F.g.h * F.g.w;
+    F.state = c->d_state;
+    F.video = 0;
+    // the last step wrote its FP32 output into d_x: scale it in place (if
+    // that step completed; otherwise the stored iterate of the last one that did)
+    F.final_iter = (d_x == c->slab_final) ? c->slab_k : -1;
+    CUDA_OR(c, launch_finish(c->prm.storage, F, (cudaStream_t)stream));
+    c->launches += 1;
+    c->last_stream = (cudaStream_t)stream;
+    return SFSEG_OK;
+}
 
 sfseg_status sfseg_get_path(const sfseg_ctx* c, int32_t* path, int32_t* fused_ctas, double* us_per_step) {
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");

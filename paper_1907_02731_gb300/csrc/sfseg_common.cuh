@@ -109,6 +109,11 @@ struct StepParams {
     int f_chan;
     const void* acc_in;
     int no_reduce;
+    // one rank's slab of a video split along t: the step's FP64 sums (of the
+    // slab's own frames) go to ext_sums[v * kRed ..] instead of updating the
+    // video's scalars; the caller sums them over the ranks and applies them
+    // with a separate finalize (null = normal finalize)
+    double* ext_sums;
 };
 
 // ---------------------------------------------------------------- storage
@@ -371,7 +376,10 @@ __device__ inline void arrive_and_finalize(const StepParams& P, int v, double* s
         __syncthreads();
         n = h;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && P.ext_sums) {
+        for (int c = 0; c < kRed; ++c) P.ext_sums[(long long)v * kRed + c] = red[c * blockDim.x];
+        P.counters[v] = 0u;
+    } else if (threadIdx.x == 0) {
         double S[kRed];
         for (int c = 0; c < kRed; ++c) S[c] = red[c * blockDim.x];
         VState* st = P.state + v;

@@ -38,7 +38,18 @@ struct PrepXParams {
     double* partials;           // [gridDim.x]
     unsigned* counter;
     double* rec_scale0;         // nullable: receives the scale of x^0 (forward record)
+    // slab of a video split along t: only frames [norm_t0, norm_t1) count in
+    // the norm, and the sum of x^2 goes to *ext_sum (the state is set later
+    // from the sum over all ranks); ext_sum null = the whole volume, state set
+    double* ext_sum;
+    int norm_t0, norm_t1;
 };
+
+// Scalar state of a slab (one rank's frames of a video split along t):
+// mode 0 starts the iteration from the global sum of x0^2 (sums[0]); mode 1
+// finalizes a power step from the global step sums (sums[0..kRed)).
+cudaError_t launch_slab_state(VState* st, const double* sums, int mode, double gain0, long long n_video,
+                              double* trace, int trace_cap, cudaStream_t s);
 
 // Up to kMax device pointers passed by value to a tiny kernel that writes
 // them into a device array (safe inside stream order, no host staging).

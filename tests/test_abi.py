@@ -106,3 +106,23 @@ def test_debug_injection_null_context(lib):
 def test_warnings_null_arguments(lib):
     flags = ctypes.c_int32(7)
     assert lib.sfseg_get_warnings(None, ctypes.byref(flags)) == sf.SFSEG_EINVAL
+
+
+def test_slab_arguments_are_checked(lib):
+    """A video split along t: the slab's own range, halo and flags are
+    validated on the host before any device call."""
+    p = sf.sfseg_default_params(8, 16, 16)
+    for lo, hi in ((3, 6), (0, 9), (2, 2), (1, 2), (-1, 4)):   # halo > rt, past the slab, empty, own < rt
+        with pytest.raises(sf.SFSegError) as ei:
+            sf.sfseg_create_slab(p, lo, hi, 8 * 16 * 16 * 4)
+        assert ei.value.status == sf.SFSEG_EINVAL
+    with pytest.raises(sf.SFSegError) as ei:
+        sf.sfseg_create_slab(p, 2, 6, 10)                       # fewer video voxels than its own frames
+    assert ei.value.status == sf.SFSEG_EINVAL
+    for flags in (sf.SFSEG_FUSED, sf.SFSEG_AUTOTUNE, sf.SFSEG_RECORD):
+        p.flags = flags
+        with pytest.raises(sf.SFSegError) as ei:
+            sf.sfseg_create_slab(p, 2, 6, 8 * 16 * 16 * 4)
+        assert ei.value.status == sf.SFSEG_EUNSUPPORTED
+    assert lib.sfseg_slab_halo_bytes(None, 0, 0) == -1
+    assert lib.sfseg_slab_step(None, None, None, None) == sf.SFSEG_EINVAL
