@@ -30,18 +30,41 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PATH_CHOICE = "auto"
 METRIC = "voxel-iterations/sec and HBM GB/s fraction at 480p vs plain FP32, rel-L2 ≤1e-3"
 UNIT = "voxel-iter/s"
 STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu
-# capture of that kernel as it stands (profiles/step_fast_video_72x480x854.md:
-# ncu --set full --clock-control none -k regex:step_fast -s 10 -c 1 ...
-# python bench.py --steps 2 --warmup 1 --no-cpu-baseline).  Only workloads
-# whose kernel was captured have an entry; the others report null.
-DRAM_TRAFFIC_PER_LAUNCH = {("video_72x480x854", "f32"): 367.805696e6 + 99.330048e6,
-                           # profiles/step_fast_bf16_video_72x480x854.md, same command with --storage bf16
-                           ("video_72x480x854", "bf16"): 181.775872e6 + 40.524288e6}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel at the workload's full size, from one ncu capture, with a
+# hash of the kernel sources the capture was taken on.  When the sources no
+# longer hash to that value the kernel has changed since the capture and the
+# figure is reported as null.
+KERNEL_SOURCES = ("paper_1907_02731_gb300/csrc/step_fast.cu", "paper_1907_02731_gb300/csrc/sfseg_common.cuh")
+DRAM_TRAFFIC_PER_LAUNCH = {
+    ("video_72x480x854", "f32"): (367908352.0 + 98473216.0, "499fb66559afb003"),
+    ("video_72x480x854", "bf16"): (181741568.0 + 40205056.0, "499fb66559afb003"),
+}
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(workload: str, storage: str):
+    """(bytes per launch, None) when captured on the current kernel sources,
+    else (None, reason)."""
+    rec = DRAM_TRAFFIC_PER_LAUNCH.get((workload, storage))
+    if rec is None:
+        return None, "not captured for this workload"
+    if rec[1] != kernel_hash():
+        return None, "kernel changed since the capture"
+    return rec[0], None
 
 
 def alu_flops_per_voxel(wl) -> int:
@@ -171,20 +194,19 @@ def rank_video_index(rank):
     return int(rank)
 
 
-def cpu_baseline(wl, frames=None):
+def cpu_baseline(wl, frames=None, iters=4):
     """The FP64 oracle as it stands, on this host's cores, over a bounded
     sample of the workload, in the workload's unit (voxel-iterations / s):
-    the video (all its frames, or the first `frames`) and 4 power steps; for
-    the batch its first video; for the differentiable form 8 frames, 4 steps
-    forward plus the oracle's reverse mode (the bench step there is forward +
-    adjoint)."""
+    the video (all its frames, or the first `frames`) and `iters` power steps;
+    for the batch its first video; for the differentiable form 8 frames,
+    `iters` steps forward plus the oracle's reverse mode (the bench step there
+    is forward + adjoint)."""
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     import oracle
     from paper_1907_02731_gb300 import inputs
     radii = (wl.rt, wl.ry, wl.rx)
     sig = (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
-    iters = 4
     if wl.name.startswith("batch"):
         nf, h, w = inputs.batch_layout()[0]
         s = inputs.make_video(nf, h, w, inputs.config_seed(inputs.BATCH_CONFIG, 0), 2)[0]
@@ -221,11 +243,13 @@ def run_reference(args, wl):
         return
     steps = []
     cb = None
-    # each step samples fewer frames when many steps are asked for, so that
-    # the whole run stays within a few minutes (about 12 full-video samples)
-    frames = max(8, (wl.nf * 12) // max(1, args.warmup + args.steps))
+    # every sample is the whole video, the same frames as the cpu_baseline
+    # leg of our arm; when many steps are asked for, each sample runs fewer
+    # power iterations, so that the whole run stays within a few minutes
+    # (about 48 full-video iterations, 2 s each on 16 cores)
+    iters = max(1, min(4, 48 // max(1, args.warmup + args.steps)))
     for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl, frames=frames)
+        cb = cpu_baseline(wl, iters=iters)
         steps.append(cb["value"])
     vals = steps[args.warmup:]
     value = statistics.median(vals)
@@ -233,7 +257,7 @@ def run_reference(args, wl):
             "steps": args.steps, "warmup": args.warmup, "impl": "reference",
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl, "f64"),
+            "config": workload_config(wl, args.storage),
             "cpu_baseline": dict(cb, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -305,6 +329,15 @@ def pipelined_calls(steps, stream, h2d, compute, d2h):
     return t0.elapsed_time(t1) / steps
 
 
+def path_flags(name: str) -> int:
+    """Context flags of a --path choice: 'auto' lets the library's autotuner
+    time the step paths on the first call (inside the warm-up) and keep the
+    fastest; the others force one path."""
+    import paper_1907_02731_gb300 as sf
+    return {"auto": sf.SFSEG_AUTOTUNE, "fast": 0, "generic": sf.SFSEG_GENERIC,
+            "fused": sf.SFSEG_FUSED}[name]
+
+
 class SingleVideo:
     """One seeded video of a named workload (FP32 / BF16 / FP16 storage); with
     several pairwise channels (Eq. 9) S is channel 0 and x0 = S."""
@@ -317,9 +350,10 @@ class SingleVideo:
         self.s = torch.from_numpy(s_np).to(dev)
         self.f = self.s if wl.nchan == 1 else torch.from_numpy(f_np).to(dev)
         self.x = torch.empty_like(self.s)
+        flags = path_flags(PATH_CHOICE) if wl.nchan == 1 else 0
         self.eng = sf.SFSeg((wl.nf, wl.h, wl.w), radii=(wl.rt, wl.ry, wl.rx),
                             sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
-                            storage=storage, nchan=wl.nchan)
+                            storage=storage, nchan=wl.nchan, flags=flags)
         self.f_host = torch.from_numpy(np.ascontiguousarray(f_np)).pin_memory()
         self.out_host = torch.empty_like(self.s, device="cpu").pin_memory()
         self.f_dev = torch.empty_like(self.f)
@@ -385,7 +419,7 @@ class Batch:
         self.xs = [torch.empty_like(t) for t in self.fs]
         self.eng = sf.SFSeg(batch_shapes=dims, radii=(wl.rt, wl.ry, wl.rx),
                             sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy), alpha=wl.alpha, p=wl.p,
-                            storage=storage)
+                            storage=storage, flags=path_flags(PATH_CHOICE))
         self.f_host = [torch.from_numpy(a).pin_memory() for a in self.f_np]
         self.out_host = [torch.empty_like(t).pin_memory() for t in self.f_host]
         self.f_dev = [torch.empty_like(t) for t in self.fs]
@@ -557,6 +591,7 @@ def run_ours(args, wl):
     for _ in range(args.warmup):
         prob.step(K)
     barrier()
+    prob.path_info = prob.eng.path() if hasattr(prob.eng, "path") else {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = prob.eng.launch_count()
     with ClockSampler(local) as clk:
@@ -623,6 +658,9 @@ def run_ours(args, wl):
     value = job_units / (ms / 1e3)
     if rank == 0:
         peak, peak_kind = _peaks()
+        traffic, traffic_note = dram_traffic(wl.name, args.storage)
+        if kind is SplitVideo or getattr(prob, "path_info", {}).get("path") not in (None, "fast"):
+            traffic, traffic_note = None, "captured for the per-step specialised kernel only"
         bpv = (3 + wl.nchan) * STORAGE_BYTES[args.storage]   # read x, sp, f_1..f_C; write y
         achieved = bpv * prob.n / (step_ms / 1e3) / 1e9
         line = {
@@ -630,14 +668,15 @@ def run_ours(args, wl):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "strong" if kind is SplitVideo else "weak",
             "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": workload_config(wl, args.storage, prob, split=args.split, world=world),
+            "config": dict(workload_config(wl, args.storage, prob, split=args.split, world=world),
+                           path=prob.path_info or ("slab steps (per-step kernels)" if kind is SplitVideo
+                                                   else "recorded per-step (specialised kernel)")),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": DRAM_TRAFFIC_PER_LAUNCH.get((wl.name, args.storage)),
+                         "traffic": traffic,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read + write)",
-                         "frac_physical": (DRAM_TRAFFIC_PER_LAUNCH[(wl.name, args.storage)]
-                                           / (step_ms / 1e3) / 1e9 / peak
-                                           if (wl.name, args.storage) in DRAM_TRAFFIC_PER_LAUNCH else None),
+                         "traffic_note": traffic_note,
+                         "frac_physical": (traffic / (step_ms / 1e3) / 1e9 / peak if traffic else None),
                          "algorithmic_bytes_per_launch": bpv * prob.n,
                          "peak_kind": peak_kind,
                          "kernel": "power step (fused stencil%s)" % (
@@ -831,7 +870,8 @@ def run_sweep(args):
         f = torch.from_numpy(f_np).cuda()
         x = torch.empty_like(f)
         eng = sf.SFSeg(shape, radii=(wl.rt, wl.ry, wl.rx), sigmas=(wl.sigma_t, wl.sigma_xy, wl.sigma_xy),
-                       alpha=wl.alpha, p=wl.p, storage=args.storage, flags=args.sweep_flags)
+                       alpha=wl.alpha, p=wl.p, storage=args.storage,
+                       flags=args.sweep_flags or path_flags(args.path))
 
         def call(k):
             x.copy_(f)
@@ -852,7 +892,8 @@ def run_sweep(args):
         step_ms = (e[0].elapsed_time(e[1]) - e[1].elapsed_time(e[2])) / reps / wl.iters
         n = int(np.prod(shape))
         line = {"sweep": "power step vs nodes", "shape": list(shape), "nodes": n,
-                "storage": args.storage, "flags": args.sweep_flags, "us_per_step": step_ms * 1e3,
+                "storage": args.storage, "flags": args.sweep_flags, "path": eng.path(),
+                "us_per_step": step_ms * 1e3,
                 "voxel_iter_per_s": n / (step_ms / 1e3),
                 "call_ms_50_steps": e[0].elapsed_time(e[1]) / reps}
         if args.sweep_sparse:
@@ -880,6 +921,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="video_72x480x854")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--path", default="auto", choices=["auto", "fast", "generic", "fused"],
+                    help="step path of the power iteration (auto: the library's autotuner)")
     ap.add_argument("--split", default=None, choices=["t"],
                     help="one video split along t over the ranks (strong scaling) instead of one "
                          "video per rank")
@@ -893,6 +936,8 @@ def main():
     ap.add_argument("--sweep-flags", type=int, default=0,
                     help="context flags for --sweep (8: force the any-radius kernel)")
     args = ap.parse_args()
+    global PATH_CHOICE
+    PATH_CHOICE = args.path
     if args.sweep:
         run_sweep(args)
         return
