@@ -358,6 +358,19 @@ int64_t sfseg_slab_halo_bytes(const sfseg_ctx* ctx, int32_t side, int32_t dir);
  * iterate (rounded to the storage type).  Errors: EINVAL, ESTATE, ECUDA. */
 sfseg_status sfseg_slab_output(sfseg_ctx* ctx, float* d_x, void* stream);
 
+/* ---- Bounds-checked build (no counterpart in the paper): the same library
+ * compiled with SFSEG_DEBUG (libsfseg_debug.so) checks, inside the kernels,
+ * every work item's range (video, frames, tile origin), the TMA box
+ * coordinates, the partials and plan slots and the offsets of the stores into
+ * the internal pitched workspace and the caller's buffers.  A failed check is
+ * counted, the first one's code (1 item range, 2 TMA coordinate, 3 store
+ * offset, 4 slot, 5 fused unit) and two values are kept, and the access is
+ * skipped: no trap.  sfseg_debug_build returns 1 in that build, 0 otherwise;
+ * sfseg_debug_status synchronises the device and returns the violations
+ * since its last call (always 0 in the normal build), clearing them. */
+int32_t sfseg_debug_build(void);
+sfseg_status sfseg_debug_status(int64_t* count, int32_t* code, int64_t* a, int64_t* b);
+
 /* Message of the last failure on ctx (ctx may be NULL: last create failure). */
 const char* sfseg_last_error(const sfseg_ctx* ctx);
 

@@ -17,7 +17,9 @@ import os
 from . import inputs  # noqa: F401  (seeded synthetic inputs)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsfseg.so")
+# SFSEG_LIBRARY=debug selects the bounds-checked build (libsfseg_debug.so)
+LIB_PATH = os.path.join(_HERE, "_build", "libsfseg_debug.so" if os.environ.get("SFSEG_LIBRARY") == "debug"
+                        else "libsfseg.so")
 
 SFSEG_OK, SFSEG_EINVAL, SFSEG_ENOMEM, SFSEG_ECUDA, SFSEG_EZERONORM = 0, 1, 2, 3, 4
 SFSEG_ENONFINITE, SFSEG_ETIMEOUT, SFSEG_EUNSUPPORTED, SFSEG_ESTATE = 5, 6, 7, 8
@@ -38,7 +40,7 @@ EXPORTS = (
     "sfseg_default_binarize", "sfseg_power_iterate_binarized", "sfseg_debug_inject_timeout",
     "sfseg_get_warnings", "sfseg_get_path", "sfseg_create_slab", "sfseg_slab_start",
     "sfseg_slab_set_norm", "sfseg_slab_step", "sfseg_slab_finish_step", "sfseg_slab_halo",
-    "sfseg_slab_halo_bytes", "sfseg_slab_output",
+    "sfseg_slab_halo_bytes", "sfseg_slab_output", "sfseg_debug_build", "sfseg_debug_status",
 )
 SFSEG_WARN_NEGATIVE_M = 1
 
@@ -114,6 +116,9 @@ def load_library(path: str = LIB_PATH):
         "sfseg_slab_halo": (_i32, [_vp, _i32, _i32, _vp, _vp]),
         "sfseg_slab_halo_bytes": (ctypes.c_int64, [_vp, _i32, _i32]),
         "sfseg_slab_output": (_i32, [_vp, _vp, _vp]),
+        "sfseg_debug_build": (_i32, []),
+        "sfseg_debug_status": (_i32, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_i32),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "sfseg_power_iterate_binarized": (_i32, [_vp, _vp, _vp, _vp, _i32,
                                                  ctypes.POINTER(sfseg_binarize), _vp, _vp]),
     }
@@ -318,6 +323,15 @@ def sfseg_slab_halo_bytes(ctx: int, side: int, direction: int) -> int:
 
 def sfseg_slab_output(ctx: int, d_x: int, stream: int = 0) -> None:
     _check(load_library().sfseg_slab_output(ctx, d_x, stream), ctx)
+
+
+def sfseg_debug_status():
+    """(violations, first code, first values) of the bounds-checked build since
+    the last call (zeros in the normal build); synchronises the device."""
+    n, code, a, b = ctypes.c_int64(), _i32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().sfseg_debug_status(ctypes.byref(n), ctypes.byref(code), ctypes.byref(a),
+                                             ctypes.byref(b)))
+    return n.value, code.value, (a.value, b.value)
 
 
 # --------------------------------------------------- torch convenience wrapper

@@ -2,7 +2,9 @@
 
 Each ``csrc/*.cu`` translation unit is compiled in parallel with
 ``nvcc -gencode arch=compute_103a,code=sm_103a -lineinfo`` and linked into
-``_build/libsfseg.so`` (static CUDA runtime, no torch types).
+``_build/libsfseg.so`` (static CUDA runtime, no torch types).  The same
+sources compiled with ``-DSFSEG_DEBUG`` give ``_build/libsfseg_debug.so``, the
+bounds-checked build (both are compiled in one parallel pass).
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsfseg.so")
+LIB_DEBUG = os.path.join(BUILD, "libsfseg_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -35,9 +38,9 @@ def _flags(verbose_ptxas: bool):
 
 
 def _stale(sources, headers) -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_DEBUG)):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_DEBUG))
     return any(os.path.getmtime(p) > t for p in sources + headers + [__file__])
 
 
@@ -51,24 +54,27 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) 
     nvcc = _nvcc()
     flags = _flags(verbose_ptxas)
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *flags, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, debug = job
+        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + (".debug.o" if debug else ".o"))
+        cmd = [nvcc, *flags, *(["-DSFSEG_DEBUG"] if debug else []), "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
-        if verbose_ptxas or not quiet:
+        if (verbose_ptxas or not quiet) and not debug:
             sys.stderr.write(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(8, len(sources))) as ex:
-        objs = list(ex.map(compile_one, sources))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, d) for d in (False, True) for src in sources]
+    with ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 2), len(jobs))) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for lib, part in ((LIB, objs[:len(sources)]), (LIB_DEBUG, objs[len(sources):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *part]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -679,6 +679,8 @@ static StepParams step_params(sfseg_ctx* c, int k, bool final_out, bool store,
     memcpy(P.gx, c->gx, sizeof c->gx);
     P.nchan = c->prm.nchan;
     P.fstride = c->total;
+    P.n_videos = c->nv;
+    P.total = c->total;
     for (int d = 0; d < 2 * kMaxRt + 1; ++d) P.gt2[d] = make_float2(P.gt[d], P.gt[d]);
     for (int d = 0; d < 2 * kMaxR + 1; ++d) {
         P.gy2[d] = make_float2(P.gy[d], P.gy[d]);
@@ -1117,8 +1119,42 @@ static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float
     return SFSEG_OK;
 }
 
+// per translation unit: the debug build's violation words (zeros otherwise)
+namespace sfseg {
+void sfseg_debug_take_fast(unsigned long long* out);
+void sfseg_debug_take_generic(unsigned long long* out);
+void sfseg_debug_take_fused(unsigned long long* out);
+}  // namespace sfseg
+
 // ======================================================================= C-ABI
 extern "C" {
+
+int32_t sfseg_debug_build(void) {
+#ifdef SFSEG_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+sfseg_status sfseg_debug_status(int64_t* count, int32_t* code, int64_t* a, int64_t* b) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(nullptr, SFSEG_ECUDA, "debug status: %s", cudaGetErrorString(e));
+    unsigned long long n = 0, first[3] = {0, 0, 0};
+    void (*take[])(unsigned long long*) = {sfseg_debug_take_fast, sfseg_debug_take_generic,
+                                           sfseg_debug_take_fused};
+    for (auto fn : take) {
+        unsigned long long w[4];
+        fn(w);
+        if (w[0] && !n) memcpy(first, w + 1, sizeof first);
+        n += w[0];
+    }
+    if (count) *count = (int64_t)n;
+    if (code) *code = (int32_t)first[0];
+    if (a) *a = (int64_t)first[1];
+    if (b) *b = (int64_t)first[2];
+    return SFSEG_OK;
+}
 
 void sfseg_default_params(sfseg_params* p, int32_t nf, int32_t h, int32_t w) {
     if (!p) return;

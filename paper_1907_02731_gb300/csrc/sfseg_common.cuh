@@ -114,7 +114,49 @@ struct StepParams {
     // video's scalars; the caller sums them over the ranks and applies them
     // with a separate finalize (null = normal finalize)
     double* ext_sums;
+    // sizes the bounds checks of the debug build compare against
+    int n_videos;
+    long long total;            // packed elements per volume array
 };
+
+// ------------------------------------------------------ debug build checks
+// Compiled with SFSEG_DEBUG (libsfseg_debug.so), kernels check segment and
+// item ranges, TMA box coordinates and workspace offsets before using them.
+// A failed check counts the violation, keeps the first one's code and two
+// values in a device word of its translation unit, and the caller skips the
+// access (no trap); sfseg_debug_status reads and clears the words.  In the
+// normal build dbg_ok is the constant true and the checks compile away.
+enum DebugCode {
+    kDbgSegment = 1,    // a work item outside its video (frames, tile origin, video index)
+    kDbgTma = 2,        // a TMA box coordinate misaligned or outside the volume's frames
+    kDbgStore = 3,      // an offset outside the packed workspace or the caller's buffer
+    kDbgSlot = 4,       // a partials / item slot outside its array
+    kDbgUnit = 5        // a fused-kernel unit outside its plan
+};
+#ifdef SFSEG_DEBUG
+static __device__ unsigned long long g_dbg[4];   // count, first code, first values (one per translation unit)
+__device__ __forceinline__ bool dbg_ok(bool ok, int code, long long a, long long b) {
+    if (!ok && atomicAdd(&g_dbg[0], 1ull) == 0ull) {
+        g_dbg[1] = (unsigned long long)code;
+        g_dbg[2] = (unsigned long long)a;
+        g_dbg[3] = (unsigned long long)b;
+    }
+    return ok;
+}
+// host: copy this translation unit's words to out[4] and clear them
+#define SFSEG_DEBUG_TU(name)                                                        \
+    void sfseg_debug_take_##name(unsigned long long* out) {                         \
+        cudaMemcpyFromSymbol(out, g_dbg, sizeof(g_dbg));                            \
+        const unsigned long long z[4] = {0, 0, 0, 0};                               \
+        cudaMemcpyToSymbol(g_dbg, z, sizeof(z));                                    \
+    }
+#else
+__device__ __forceinline__ bool dbg_ok(bool ok, int, long long, long long) { return true; }
+#define SFSEG_DEBUG_TU(name)                                                        \
+    void sfseg_debug_take_##name(unsigned long long* out) {                         \
+        for (int i = 0; i < 4; ++i) out[i] = 0;                                     \
+    }
+#endif
 
 // ---------------------------------------------------------------- storage
 __device__ __forceinline__ float to_f(float v) { return v; }

@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     for (int sg = seg_b; sg < seg_e; ++sg) {
         const WorkItem it = P.items[sg];
         const int v = it.video;
+        if (!dbg_ok(sg < P.n_items && v >= 0 && v < P.n_videos, kDbgSlot, sg, v)) continue;
         if (v != run_v) {
             __syncthreads();   // every thread has read the previous run's scalars
             if (tid == 0) {
@@ -370,6 +371,13 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
         if (s_skip) continue;
         const VideoGeom g = P.geo[v];
         const int ta = it.t0, tb = it.t1, x0 = it.x0, y0 = it.y0;
+        // (uniform over the CTA: every thread skips the same segment)
+        if (!dbg_ok(0 <= ta && ta < tb && tb <= g.nf && 0 <= x0 && x0 < g.w && 0 <= y0 && y0 < g.h,
+                    kDbgSegment, sg, ((long long)ta << 32) | (unsigned)tb))
+            continue;
+        if (!dbg_ok(((x0 - XPAD) * (int)sizeof(TS)) % 16 == 0 && g.off + (long long)g.nf * g.plane <= P.total,
+                    kDbgTma, x0, g.off))
+            continue;
         const int t_end = tb + RT;
         const int p_first = max(ta - RT, 0), p_last = min(t_end, g.nf);   // valid frames [p_first, p_last)
         const int n_valid = p_last - p_first;
@@ -461,6 +469,7 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const int yy = y0 + brow;
             const int xg = x0 + 4 * lane;
             const bool st_ok = out_lane && yy < g.h;
+            bool st_ok_dbg = true;   // the debug build's store check (always true otherwise)
 
             float2 rab[NR][4];   // temporal ring of the (a, b) pair
             float rc[NR][4];     // temporal ring of c
@@ -547,7 +556,11 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                         Vec4<float>::store(P.aux_k + ao, ak);
                         Vec4<float>::store(P.aux_f + ao, af);
                     }
-                    if (st_ok) {
+                    const long long zoff = (long long)o * g.plane + (long long)yy * g.pitch + xg;
+                    if (st_ok && xg < g.pitch &&   // the lanes that store
+                        !dbg_ok(zoff + 3 < (long long)g.nf * g.plane, kDbgStore, zoff, g.nf))
+                        st_ok_dbg = false;
+                    if (st_ok && st_ok_dbg) {
                         if (FO) {
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
@@ -646,6 +659,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
 }
 
 }  // namespace fast
+
+SFSEG_DEBUG_TU(fast)
 
 // --------------------------------------------------------------- host side
 struct FastEntry {

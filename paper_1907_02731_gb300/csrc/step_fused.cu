@@ -160,10 +160,12 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
         for (int u = blockIdx.x; u < F.n_units1; u += G) {
             const int v = unit_video(F.unit1_begin, F.n_videos, u);
             const VideoGeom g = P.geo[v];
+            if (!dbg_ok(g.off + (long long)g.nf * g.plane <= F.total, kDbgUnit, u, v)) continue;
             const int ntx = (g.w + FU_TX - 1) / FU_TX, nty = (g.h + FU_TY - 1) / FU_TY;
             const int local = u - F.unit1_begin[v];
             const int t = local / (ntx * nty), r = local - t * (ntx * nty);
             const int y0 = (r / ntx) * FU_TY, x0 = (r - (r / ntx) * ntx) * FU_TX;
+            if (!dbg_ok(t < g.nf && y0 < g.h && x0 < g.w, kDbgUnit, u, t)) continue;   // uniform over the CTA
             const TS* Xv = X + g.off;
             const TS* SPv = (const TS*)P.sp + g.off;
             const TS* Fv = (const TS*)P.f + g.off;
@@ -299,6 +301,7 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
             for (int it = ib; it < ie; ++it) {
                 const WorkItem item = P.items[it];
                 const int v = item.video;
+                if (!dbg_ok(it < P.n_items && v >= 0 && v < F.n_videos, kDbgSlot, it, v)) continue;
                 __syncthreads();   // s_* of the previous item are no longer read
                 if (threadIdx.x == 0 && F.n_videos > 1) {
                     const VState* st = P.state + v;
@@ -313,6 +316,9 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
                 const VideoGeom g = P.geo[v];
                 const int rows = fused_rows2(g.w);
                 const int nchunk = (g.h + rows - 1) / rows;
+                if (!dbg_ok(0 <= item.t0 && item.t0 <= item.t1 && item.t1 <= g.nf * nchunk, kDbgUnit, it,
+                            item.t1))
+                    continue;
                 const TS* Xv = X + g.off;
                 const TS* SPv = (const TS*)P.sp + g.off;
                 const TS* Fv = (const TS*)P.f + g.off;
@@ -397,6 +403,8 @@ timed_out:
             P.state[v].done = 1;
         }
 }
+
+SFSEG_DEBUG_TU(fused)
 
 size_t fused_smem_bytes(int ry, int rx) {
     const size_t TXH = FU_TX + 2 * rx, TYH = FU_TY + 2 * ry;

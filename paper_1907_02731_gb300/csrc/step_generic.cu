@@ -34,6 +34,7 @@ step_generic_kernel(const __grid_constant__ StepParams P)
     extern __shared__ __align__(16) float sm[];
     const WorkItem it = P.items[blockIdx.x];
     const int v = it.video;
+    if (!dbg_ok((int)blockIdx.x < P.n_items && v >= 0 && v < P.n_videos, kDbgSlot, blockIdx.x, v)) return;
     VState* st = P.state + v;
     __shared__ int s_skip;
     __shared__ float s_scale, s_gain, s_shift;
@@ -47,6 +48,10 @@ step_generic_kernel(const __grid_constant__ StepParams P)
     if (s_skip) return;
 
     const VideoGeom g = P.geo[v];
+    if (!dbg_ok(0 <= it.t0 && it.t0 < it.t1 && it.t1 <= g.nf && 0 <= it.x0 && it.x0 < g.w && 0 <= it.y0 &&
+                    it.y0 < g.h && g.off + (long long)g.nf * g.plane <= P.total,
+                kDbgSegment, blockIdx.x, ((long long)it.t0 << 32) | (unsigned)it.t1))
+        return;
     const int rt = P.rt, ry = P.ry, rx = P.rx;
     constexpr int TX = GT_TX, TY = GT_TY;
     const int TXH = TX + 2 * rx, TYH = TY + 2 * ry, NR = 2 * rt + 1;
@@ -150,6 +155,7 @@ step_generic_kernel(const __grid_constant__ StepParams P)
                     for (int k = 0; k < NCH; ++k) cs[k] = fmaf(gw, sl[k * RS + idx], cs[k]);
                 }
                 const long long o = (long long)to * g.plane + (long long)yy * g.pitch + xg;
+                if (!dbg_ok(o < (long long)g.nf * g.plane, kDbgStore, o, g.nf)) continue;
                 const float s = to_f(SP[o]);
                 const float xh = scale * to_f(X[o]);
                 float inner;
@@ -191,6 +197,8 @@ step_generic_kernel(const __grid_constant__ StepParams P)
         for (int c = 0; c < kRed; ++c) P.partials[(long long)blockIdx.x * kRed + c] = acc[c];
     arrive_and_finalize(P, v, sh);
 }
+
+SFSEG_DEBUG_TU(generic)
 
 size_t generic_smem_bytes(int rt, int ry, int rx, int nchan) {
     const size_t nch = (size_t)nchan + 2;

@@ -19,3 +19,17 @@ def cuda_device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+@pytest.fixture(autouse=True)
+def _debug_build_clean(request):
+    """Under the bounds-checked build (SFSEG_LIBRARY=debug) every GPU test must
+    leave no recorded violation (item ranges, TMA coordinates, workspace
+    offsets)."""
+    yield
+    if os.environ.get("SFSEG_LIBRARY") != "debug" or request.node.get_closest_marker("gpu") is None:
+        return
+    import paper_1907_02731_gb300 as sf
+    assert sf.load_library().sfseg_debug_build() == 1
+    n, code, vals = sf.sfseg_debug_status()
+    assert n == 0, f"debug build: {n} bounds violations, first code {code} values {vals}"

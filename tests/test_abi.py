@@ -126,3 +126,17 @@ def test_slab_arguments_are_checked(lib):
         assert ei.value.status == sf.SFSEG_EUNSUPPORTED
     assert lib.sfseg_slab_halo_bytes(None, 0, 0) == -1
     assert lib.sfseg_slab_step(None, None, None, None) == sf.SFSEG_EINVAL
+
+
+def test_debug_build_exports_the_same_entry_points():
+    """The bounds-checked build (libsfseg_debug.so) is built beside the library
+    and exports every entry point of include/sfseg.h; it says which it is."""
+    import ctypes
+    import os
+    path = os.path.join(os.path.dirname(sf.LIB_PATH), "libsfseg_debug.so")
+    L = ctypes.CDLL(path)
+    for name in sf.EXPORTS:
+        assert hasattr(L, name), name
+    L.sfseg_debug_build.restype = ctypes.c_int32
+    assert L.sfseg_debug_build() == 1
+    assert sf.load_library().sfseg_debug_build() == (1 if os.environ.get("SFSEG_LIBRARY") == "debug" else 0)

@@ -159,6 +159,31 @@ def test_fullsize_low_precision_fifty_steps(cuda_device, video, storage):
     assert rel_l2(out[storage], out["f32"]) < TOL_LOWP
 
 
+@pytest.mark.parametrize("storage,ulp", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
+def test_crop_low_precision_iterate_matches_oracle(cuda_device, video, storage, ulp):
+    """The precision form on full-resolution frames: the first 16 frames of
+    the 854x480 video, 11x11x5 Gaussian, 20 steps with BF16/FP16 storage,
+    against the FP64 oracle fed the same rounded sp, f and x0.  Relative L2
+    within the 1e-3 bar; max-abs within four storage units in the last place
+    of the largest entry (the iterate is stored rounded between steps; the
+    last step writes FP32)."""
+    import torch
+    crop = np.ascontiguousarray(video[:16])
+    sp, fr = _rounded_inputs(crop, storage)
+    K = 20
+    eng = sf.SFSeg(crop.shape, radii=RADII, sigmas=SIG, alpha=WL.alpha, p=WL.p, storage=storage,
+                   flags=sf.SFSEG_S_IS_SP)
+    x = eng.power_iterate(to_dev(sp), to_dev(fr), to_dev(fr), K).cpu().numpy().astype(np.float64)
+    tr = eng.trace()
+    eng.close()
+    torch.cuda.synchronize()
+    ref = oracle.power_iterate(sp.astype(np.float64), fr.astype(np.float64), fr.astype(np.float64), K,
+                               RADII, SIG, WL.alpha)
+    assert rel_l2(x, ref["x"]) < TOL_LOWP
+    assert np.abs(x - ref["x"]).max() < 4 * ulp * np.abs(ref["x"]).max()
+    np.testing.assert_allclose(tr["rayleigh"], ref["rayleigh"], rtol=1e-3)
+
+
 def test_fullsize_two_channels_sampled_one_step(cuda_device):
     """Eq. 9 with the 2-channel workload (854x480x72, S = channel 0): y = M S
     at 4096 sampled voxels plus corners and edges against the oracle's
