@@ -43,8 +43,8 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # figure is reported as null.
 KERNEL_SOURCES = ("paper_1907_02731_gb300/csrc/step_fast.cu", "paper_1907_02731_gb300/csrc/sfseg_common.cuh")
 DRAM_TRAFFIC_PER_LAUNCH = {
-    ("video_72x480x854", "f32"): (367908352.0 + 98473216.0, "499fb66559afb003"),
-    ("video_72x480x854", "bf16"): (181741568.0 + 40205056.0, "499fb66559afb003"),
+    ("video_72x480x854", "f32"): (367756800.0 + 98738688.0, "7db2f10bf580201d"),
+    ("video_72x480x854", "bf16"): (181803520.0 + 40122624.0, "7db2f10bf580201d"),
 }
 
 
@@ -195,13 +195,14 @@ def rank_video_index(rank):
     return int(rank)
 
 
-def cpu_baseline(wl, frames=None, iters=4):
+def cpu_baseline(wl, frames=None, iters=4, min_seconds=5.0):
     """The FP64 oracle as it stands, on this host's cores, over a bounded
     sample of the workload, in the workload's unit (voxel-iterations / s):
-    the video (all its frames, or the first `frames`) and `iters` power steps;
-    for the batch its first video; for the differentiable form 8 frames,
-    `iters` steps forward plus the oracle's reverse mode (the bench step there
-    is forward + adjoint)."""
+    the video (all its frames, or the first `frames`) and `iters` power steps
+    (more when that takes under `min_seconds`, so that small volumes are timed
+    over a few seconds); for the batch its first video; for the
+    differentiable form 8 frames, `iters` steps forward plus the oracle's
+    reverse mode (the bench step there is forward + adjoint)."""
     threads = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(threads))
     import oracle
@@ -224,14 +225,21 @@ def cpu_baseline(wl, frames=None, iters=4):
     sub = np.ascontiguousarray(s[:nf_s], dtype=np.float64)
     fsub = np.ascontiguousarray(f[..., :nf_s, :, :], dtype=np.float64)
     sp = oracle.unary(sub, wl.p)
-    t0 = time.perf_counter()
+
+    def run(k):
+        t0 = time.perf_counter()
+        if grad:
+            target = (sub > 0.5).astype(np.float64)
+            oracle.adjoint(sp, fsub, sub, k, radii, sig, wl.alpha, target)
+        else:
+            oracle.power_iterate(sp, fsub, sub, k, radii, sig, wl.alpha)
+        return time.perf_counter() - t0
+    dt = run(iters)
+    if dt < min_seconds:   # small volumes: enough steps for a few seconds of CPU work
+        iters = min(4000, max(iters + 1, int(iters * min_seconds / max(dt, 1e-4))))
+        dt = run(iters)
     if grad:
-        target = (sub > 0.5).astype(np.float64)
-        oracle.adjoint(sp, fsub, sub, iters, radii, sig, wl.alpha, target)
         what = f"the first {nf_s} frames of " + what + ", forward + reverse mode"
-    else:
-        oracle.power_iterate(sp, fsub, sub, iters, radii, sig, wl.alpha)
-    dt = time.perf_counter() - t0
     vox_iter = sub.size * iters
     return {"value": vox_iter / dt, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
             "kind": "oracle",
