@@ -392,8 +392,9 @@ static void build_fused_plan(const std::vector<VideoGeom>& geo, int G, FusedPlan
     fp->item_begin.push_back((int)fp->vseg.size());
 }
 
-// CTAs worth launching: no more than the resident maximum, nor than the
-// larger phase's unit count.
+// CTAs worth launching: one per phase-1 unit plus one spare per video (the
+// last CTAs run the videos' scalar updates while the others filter the next
+// step), or one per phase-2 unit if more; no more than the resident maximum.
 static int fused_default_ctas(const sfseg_ctx* c) {
     int tx, ty, nt;
     fused_tile(&tx, &ty, &nt);
@@ -402,6 +403,7 @@ static int fused_default_ctas(const sfseg_ctx* c) {
         u1 += (long long)g.nf * ((g.h + ty - 1) / ty) * ((g.w + tx - 1) / tx);
         u2 += fused_units2(g);
     }
+    u1 += c->nv;
     long long n = u1 > u2 ? u1 : u2;
     if (n > c->fused_max) n = c->fused_max;
     return n < 1 ? 1 : (int)n;

@@ -18,7 +18,7 @@
 //            buffer after the last step) and the FP32/FP64 partial sums of
 //            z.z, x.z, x.x, |z - s x|^2, one FP64 record per CTA and video;
 //   barrier
-//   finalize CTA v mod G sums video v's records in a fixed order and updates
+//   finalize CTA G-1-(v mod G) sums video v's records in a fixed order and updates
 //            its scalars (Rayleigh quotient, residual, norm, next scale and
 //            gain: the same finish_step as the per-step kernels), while the
 //            other CTAs start the next phase 1 (which needs no scalars); the
@@ -390,9 +390,12 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
             }
         }
         if (!grid_barrier(F.bar, G, nb, false)) goto timed_out;
-        // finalize: CTA v mod G updates video v; the next phase 1 needs no
-        // scalars, and the next phase 2 starts after the next barrier
-        for (int v = blockIdx.x; v < F.n_videos; v += G) fused_finalize(P, v, reinterpret_cast<double*>(sm));
+        // finalize: CTA G - 1 - (v mod G) updates video v -- the last CTAs,
+        // which have no phase-1 unit when the grid has a spare CTA per video,
+        // so the update overlaps the other CTAs' next phase 1 (which needs no
+        // scalars); the next phase 2 starts after the next barrier
+        for (int v = (int)G - 1 - (int)blockIdx.x; v < F.n_videos; v += G)
+            fused_finalize(P, v, reinterpret_cast<double*>(sm));
     }
     return;
 

@@ -210,3 +210,35 @@ def test_autotune_batched_matches_oracle(cuda_device):
     for f, xb in zip(fs, xs):
         ref = oracle_power(f, f, 8, radii, sig, 1.0, 0.1)
         assert rel_l2(xb.cpu().numpy(), ref["x"]) < TOL_F32
+
+
+def test_autotuned_context_serves_every_entry_point(cuda_device):
+    """After the autotuner kept the fused launch, the per-step entry points of
+    the same context (Rayleigh quotient, one application of M, the binarised
+    iteration) still run their one-launch-per-step kernels and match the
+    oracle."""
+    import torch
+    from oracle import binarize
+    rng = np.random.default_rng(15)
+    shape, radii, sig = (6, 24, 40), (2, 5, 5), (1.5, 3.0, 3.0)
+    f = rng.random(shape, dtype=np.float32)
+    eng = sf.SFSeg(shape, radii=radii, sigmas=sig, alpha=1.0, p=0.1, flags=sf.SFSEG_AUTOTUNE)
+    try:
+        d = to_dev(f)
+        x = eng.power_iterate(d, d, d.clone(), 10)
+        torch.cuda.synchronize()
+        assert eng.path()["path"] in ("fast", "fused")
+        ref = oracle_power(f, f, 10, radii, sig, 1.0, 0.1)
+        assert rel_l2(x.cpu().numpy(), ref["x"]) < TOL_F32
+        xv = rng.standard_normal(shape).astype(np.float32)
+        y = eng.apply(to_dev(xv)).cpu().numpy()
+        sp = oracle.unary(f, 0.1)
+        assert rel_l2(y, oracle.apply_M(sp, f, xv, radii, sig, 1.0)) < 1e-6
+        lam, _ = eng.rayleigh(to_dev(f))
+        r1 = oracle.power_iterate(sp, f, f, 1, radii, sig, 1.0)
+        assert abs(lam - r1["rayleigh"][0]) < 1e-6 * abs(r1["rayleigh"][0])
+        xb, mask = eng.power_iterate_binarized(d, d, d.clone(), 6, k0=3)
+        rb = binarize.power_iterate_binarized(sp, f, f, 6, radii, sig, 1.0, 3, 10.0, 0.5, 0.5)
+        assert rel_l2(xb.cpu().numpy(), rb["x"]) < 1e-5 * 2.5 ** 3
+    finally:
+        eng.close()

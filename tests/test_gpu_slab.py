@@ -119,12 +119,13 @@ def test_split_video_matches_oracle(cuda_device, shape, radii, sig, world):
                                atol=1e-5 * ref["rayleigh"][-1])
 
 
-def test_split_video_bf16_matches_oracle(cuda_device):
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_split_video_low_precision_matches_oracle(cuda_device, storage):
     rng = np.random.default_rng(5)
     shape, radii, sig = (20, 36, 52), (2, 5, 5), (1.5, 3.0, 3.0)
     f = rng.random(shape, dtype=np.float32)
-    x, _ = run_split(f, f, f, 8, 3, radii, sig, 1.0, 0.1, storage="bf16")
-    ref = oracle_power(f, f, 8, radii, sig, 1.0, 0.1, storage="bf16")
+    x, _ = run_split(f, f, f, 8, 3, radii, sig, 1.0, 0.1, storage=storage)
+    ref = oracle_power(f, f, 8, radii, sig, 1.0, 0.1, storage=storage)
     assert rel_l2(x, ref["x"]) < TOL_LOWP
 
 
