@@ -18,14 +18,16 @@
 //            buffer after the last step) and the FP32/FP64 partial sums of
 //            z.z, x.z, x.x, |z - s x|^2, one FP64 record per CTA and video;
 //   barrier
-//   finalize CTA G-1-(v mod G) sums video v's records in a fixed order and updates
-//            its scalars (Rayleigh quotient, residual, norm, next scale and
-//            gain: the same finish_step as the per-step kernels), while the
-//            other CTAs start the next phase 1 (which needs no scalars); the
-//            next phase 2 reads them after the next barrier.
+//   finalize CTA G - 1 - (v mod G) sums video v's records in a fixed order
+//            and updates its scalars (Rayleigh quotient, residual, norm, next
+//            scale and gain: the same finish_step as the per-step kernels),
+//            while the other CTAs start the next phase 1 (which needs no
+//            scalars); the next phase 2 reads them after the next barrier.
 //
-// Videos that converged (or failed) skip their units; when all have, every
-// CTA leaves the loop together (they read the same final scalars).  Each
+// Videos that converged (or failed) skip their phase-2 units (phase 1 filters
+// them once more into the scratch, which nothing reads); when all have, every
+// CTA leaves the loop together after the first barrier (they read the same
+// settled scalars).  Each
 // barrier wait is limited in time: a CTA that gives up raises a grid-wide
 // abort flag, marks every video SFSEG_ETIMEOUT and returns; the other CTAs see
 // the flag (or their own limit) and return too.  No trap, no unbounded wait.
