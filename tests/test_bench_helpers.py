@@ -11,3 +11,19 @@ def test_alu_flops_per_voxel():
     wl2 = inputs.WORKLOADS["video2ch_72x480x854"]
     assert wl2.nchan == 2
     assert bench.alu_flops_per_voxel(wl2) == 5 + 2 * 4 * 27 + 16 + 10
+
+
+def test_clock_summary_parses_samples_and_reasons():
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2040, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"] and "window" not in s
+    c.after = True                     # only a sample taken after a short timed region
+    assert "first sample after" in c.summary()["window"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
