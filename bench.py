@@ -43,8 +43,8 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # figure is reported as null.
 KERNEL_SOURCES = ("paper_1907_02731_gb300/csrc/step_fast.cu", "paper_1907_02731_gb300/csrc/sfseg_common.cuh")
 DRAM_TRAFFIC_PER_LAUNCH = {
-    ("video_72x480x854", "f32"): (367756800.0 + 98738688.0, "7db2f10bf580201d"),
-    ("video_72x480x854", "bf16"): (181803520.0 + 40122624.0, "7db2f10bf580201d"),
+    ("video_72x480x854", "f32"): (367783936.0 + 99002112.0, "ef275f019e593a7c"),
+    ("video_72x480x854", "bf16"): (181752320.0 + 40438784.0, "ef275f019e593a7c"),
 }
 
 

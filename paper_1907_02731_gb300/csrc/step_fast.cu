@@ -156,6 +156,38 @@ template <> struct Vec4<__half> {
 };
 
 template <typename TS> struct Ld2;
+// b0 = sp * x for a column pair of the y-pass.  The product of two BF16 or
+// FP16 values is exact in FP32, so the mixed-precision FMA (2-byte operands,
+// FP32 addend and result; the addend -0 keeps the product's sign of zero)
+// gives the same value as converting both operands and multiplying in FP32,
+// without the four conversions (measured: 207.6 -> 201.0 us per step for
+// BF16 storage at 854x480x72, bit-identical iterates).
+template <typename TS> struct Prod2;
+template <> struct Prod2<float> {
+    __device__ static float2 get(const float* sp, const float* x) {
+        return __fmul2_rn(*reinterpret_cast<const float2*>(sp), *reinterpret_cast<const float2*>(x));
+    }
+};
+template <> struct Prod2<__nv_bfloat16> {
+    __device__ static float2 get(const __nv_bfloat16* sp, const __nv_bfloat16* x) {
+        const unsigned us = *reinterpret_cast<const unsigned*>(sp), ux = *reinterpret_cast<const unsigned*>(x);
+        float lo, hi;
+        asm("{\n .reg .b16 s0, s1, x0, x1;\n mov.b32 {s0, s1}, %2;\n mov.b32 {x0, x1}, %3;\n"
+            " fma.rn.f32.bf16 %0, s0, x0, %4;\n fma.rn.f32.bf16 %1, s1, x1, %4;\n}"
+            : "=f"(lo), "=f"(hi) : "r"(us), "r"(ux), "f"(-0.0f));
+        return make_float2(lo, hi);
+    }
+};
+template <> struct Prod2<__half> {
+    __device__ static float2 get(const __half* sp, const __half* x) {
+        const unsigned us = *reinterpret_cast<const unsigned*>(sp), ux = *reinterpret_cast<const unsigned*>(x);
+        float lo, hi;
+        asm("{\n .reg .b16 s0, s1, x0, x1;\n mov.b32 {s0, s1}, %2;\n mov.b32 {x0, x1}, %3;\n"
+            " fma.rn.f32.f16 %0, s0, x0, %4;\n fma.rn.f32.f16 %1, s1, x1, %4;\n}"
+            : "=f"(lo), "=f"(hi) : "r"(us), "r"(ux), "f"(-0.0f));
+        return make_float2(lo, hi);
+    }
+};
 template <> struct Ld2<float> {
     __device__ static float2 get(const float* p) { return *reinterpret_cast<const float2*>(p); }
 };
@@ -426,10 +458,8 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     float2 q0[C::TROWS], q1[C::TROWS], q2[C::TROWS];
 #pragma unroll
                     for (int i = 0; i < C::IN_ROWS; ++i) {
-                        const float2 xv = Ld2<TS>::get(sx + i * BOXW);
-                        const float2 sv = Ld2<TS>::get(ssp + i * BOXW);
                         const float2 fv = Ld2<TS>::get(sf + i * BOXW);
-                        const float2 b0 = __fmul2_rn(sv, xv);
+                        const float2 b0 = Prod2<TS>::get(ssp + i * BOXW, sx + i * BOXW);
                         const float2 b1 = __fmul2_rn(fv, b0);
                         const float2 b2 = __fmul2_rn(fv, b1);
 #pragma unroll
