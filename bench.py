@@ -43,8 +43,8 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # figure is reported as null.
 KERNEL_SOURCES = ("paper_1907_02731_gb300/csrc/step_fast.cu", "paper_1907_02731_gb300/csrc/sfseg_common.cuh")
 DRAM_TRAFFIC_PER_LAUNCH = {
-    ("video_72x480x854", "f32"): (367783936.0 + 99002112.0, "ef275f019e593a7c"),
-    ("video_72x480x854", "bf16"): (181752320.0 + 40438784.0, "ef275f019e593a7c"),
+    ("video_72x480x854", "f32"): (367868160.0 + 98770432.0, "bb6a333506814249"),
+    ("video_72x480x854", "bf16"): (181694208.0 + 39856384.0, "bb6a333506814249"),
 }
 
 

@@ -14,7 +14,8 @@
 //   load    one thread issues three TMA 3D box loads (x, sp, f) of the tile
 //           plus its halo (128 x (12 + 2 RY)) into a ring of RT + NYB + LA
 //           shared-memory stages (zero fill outside the volume = the zero
-//           padding of Eq. 7's convolutions), LA frames ahead, completion on
+//           padding of Eq. 7's convolutions), LA frames ahead (1 for FP32
+//           storage, 2 for 2-byte storage), completion on
 //           an mbarrier per stage;
 //   y-pass  warps 0..3 ("A"): a task is a column pair x 6 output rows;
 //           a0 = sp x, a1 = f a0, a2 = f a1 and the vertical taps in
@@ -54,7 +55,6 @@ namespace fast {
 constexpr int TX = 112, TY = 12, XPAD = 8, BOXW = TX + 2 * XPAD, YBW = BOXW;
 constexpr int NA_WARPS = 4;                   // warps running the loads and the y-pass
 constexpr int NT = 32 * (NA_WARPS + TY);      // plus one x-pass/combine warp per tile row
-constexpr int LA = 1;                         // frames of TMA lookahead
 constexpr unsigned long long kWaitNs = 1000000000ull;   // a device-side wait gives up after 1 s
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -216,6 +216,10 @@ struct Cfg {
     // y-pass output buffers: the x-pass warps may trail the y-pass by NYB - 1
     // frames (with 2-byte storage the stages are small enough for four)
     static constexpr int NYB = sizeof(TS) == 4 ? 2 : 4;
+    // frames of TMA lookahead: the 2-byte stages leave room for two (measured
+    // at 854x480x72, BF16: 201.0 -> 193.9 us per step; FP32 gains nothing
+    // from a second frame and has no room for it)
+    static constexpr int LA = sizeof(TS) == 4 ? 1 : 2;
     static constexpr int NS = RT + NYB + LA;                  // stages (see the stage-reuse note)
     static constexpr int BOX_BYTES = ROWS * BOXW * (int)sizeof(TS);
     static constexpr int ARR = (BOX_BYTES + 127) / 128 * 128; // one array of a stage
@@ -438,14 +442,14 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
             const bool a_task = tid < C::NTA;
             const float2* gy2 = P.gy2;
             if (tid == 0)
-                for (int q = 0; q < LA && q < n_valid; ++q) issue(p_first + q);
+                for (int q = 0; q < C::LA && q < n_valid; ++q) issue(p_first + q);
             for (int vc = 0; vc < n_valid; ++vc) {
                 const int p = p_first + vc;
                 const int b = (int)((unsigned)vc % C::NYB);
                 const unsigned n = (unsigned)vc / C::NYB;
                 if (n >= 1 && !mbar_wait(smem_u32(&empty[b]), ((emptybase >> b) ^ (n - 1)) & 1u, &s_abort))
                     give_up(v);
-                if (tid == 0 && !s_abort && vc + LA < n_valid) issue(p + LA);
+                if (tid == 0 && !s_abort && vc + C::LA < n_valid) issue(p + C::LA);
                 const int s = p % NS;
                 if (mbar_wait(smem_u32(&bars[s]), parity(p), &s_abort)) owed &= ~(1u << s);
                 else give_up(v);   // the load stays owed: drained before the CTA leaves
