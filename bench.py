@@ -360,7 +360,7 @@ def path_flags(name: str) -> int:
     fastest; the others force one path."""
     import paper_1907_02731_gb300 as sf
     return {"auto": sf.SFSEG_AUTOTUNE, "fast": 0, "generic": sf.SFSEG_GENERIC,
-            "fused": sf.SFSEG_FUSED}[name]
+            "fused": sf.SFSEG_FUSED, "cluster": sf.SFSEG_CLUSTER}[name]
 
 
 class SingleVideo:
@@ -977,7 +977,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="video_72x480x854")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f16"])
-    ap.add_argument("--path", default="auto", choices=["auto", "fast", "generic", "fused"],
+    ap.add_argument("--path", default="auto", choices=["auto", "fast", "generic", "fused", "cluster"],
                     help="step path of the power iteration (auto: the library's autotuner)")
     ap.add_argument("--split", default=None, choices=["t"],
                     help="one video split along t over the ranks (strong scaling) instead of one "

@@ -65,7 +65,8 @@ enum {
     SFSEG_RECORD = 4,        /* record checkpoints during power_iterate for sfseg_adjoint */
     SFSEG_GENERIC = 8,       /* force the generic (any-radius) stencil kernel */
     SFSEG_FUSED = 16,        /* power_iterate runs all its steps in one launch (see below) */
-    SFSEG_AUTOTUNE = 32      /* power_iterate chooses its step path by timing (see below) */
+    SFSEG_AUTOTUNE = 32,     /* power_iterate chooses its step path by timing (see below) */
+    SFSEG_CLUSTER = 64       /* power_iterate runs in one thread-block cluster (see below) */
 };
 
 /* Step paths of sfseg_power_iterate(_batched) (the loop of Algorithm 1, one
@@ -81,9 +82,22 @@ enum {
  *                       barrier.  Meant for small volumes (whose fixed per-step
  *                       launch cost dominates); one channel only; every
  *                       barrier wait gives up after 1 s with SFSEG_ETIMEOUT.
+ *   SFSEG_PATH_CLUSTER  all K steps in one thread-block cluster of up to 16
+ *                       CTAs that keeps the whole video (sp, f, the iterate,
+ *                       the filtered channels) in shared memory: 16-column
+ *                       tiles of all frames per CTA, the neighbours' halo
+ *                       read through distributed shared memory, one cluster
+ *                       barrier per step, the norm update repeated in every
+ *                       CTA from the same records.  One video, one channel,
+ *                       radii (3,3,3), (2,5,5) or (2,4,4), at most 16 tiles
+ *                       whose frames fit one CTA's shared memory (e.g. a
+ *                       64x64 video of 16 frames at (3,3,3)); no internal
+ *                       scratch; nothing to time out (no spin-wait).
  * Default: FAST where the radii are specialised, else GENERIC; SFSEG_FUSED
  * selects FUSED (SFSEG_EUNSUPPORTED for nchan > 1, with SFSEG_RECORD, or on a
- * device without cooperative launch).  SFSEG_AUTOTUNE: the first
+ * device without cooperative launch); SFSEG_CLUSTER selects CLUSTER
+ * (SFSEG_EUNSUPPORTED where the video does not qualify or the device cannot
+ * schedule the cluster).  SFSEG_AUTOTUNE: the first
  * power_iterate call on the context times each path it can run (and the fused
  * launch at three grid sizes, when the volume has at most 8 Mi voxels) on the
  * context's own features and x0, keeps the fastest and caches the choice per
@@ -95,7 +109,8 @@ enum {
 typedef enum {
     SFSEG_PATH_FAST = 0,
     SFSEG_PATH_GENERIC = 1,
-    SFSEG_PATH_FUSED = 2
+    SFSEG_PATH_FUSED = 2,
+    SFSEG_PATH_CLUSTER = 3
 } sfseg_path;
 
 typedef struct {
@@ -308,7 +323,7 @@ sfseg_status sfseg_power_iterate_noalloc(const sfseg_params* prm, const float* d
  * least rt frames (a halo then comes from one neighbour); video_voxels: the
  * voxel count of the whole video (it sets the storage gain, the same on
  * every rank).  Errors: EINVAL, EUNSUPPORTED (SFSEG_FUSED, SFSEG_AUTOTUNE,
- * SFSEG_RECORD), ENOMEM, ECUDA. */
+ * SFSEG_RECORD, SFSEG_CLUSTER), ENOMEM, ECUDA. */
 sfseg_status sfseg_create_slab(const sfseg_params* prm, int32_t own_lo, int32_t own_hi,
                                int64_t video_voxels, sfseg_ctx** out);
 
@@ -397,9 +412,10 @@ int32_t sfseg_plan_segments(int32_t n_videos, const int32_t* dims, int32_t n_sms
 int64_t sfseg_launch_count(const sfseg_ctx* ctx);
 
 /* The step path power_iterate uses (sfseg_path; with SFSEG_AUTOTUNE, the one
- * chosen by the first call), the CTA count of the fused launch (0 for the
- * per-step paths) and, nullable, us_per_step[3]: the microseconds per step the
- * autotuner measured for each path (index = sfseg_path; -1 where not timed).
+ * chosen by the first call), the CTA count of the fused or cluster launch (0
+ * for the per-step paths) and, nullable, us_per_step[4]: the microseconds per
+ * step the autotuner measured for each path (index = sfseg_path; -1 where not
+ * timed).
  * No device access.  Errors: EINVAL. */
 sfseg_status sfseg_get_path(const sfseg_ctx* ctx, int32_t* path, int32_t* fused_ctas,
                             double* us_per_step);

@@ -25,9 +25,10 @@ SFSEG_OK, SFSEG_EINVAL, SFSEG_ENOMEM, SFSEG_ECUDA, SFSEG_EZERONORM = 0, 1, 2, 3,
 SFSEG_ENONFINITE, SFSEG_ETIMEOUT, SFSEG_EUNSUPPORTED, SFSEG_ESTATE = 5, 6, 7, 8
 SFSEG_F32, SFSEG_BF16, SFSEG_F16 = 0, 1, 2
 SFSEG_S_IS_SP, SFSEG_NO_GRAPH, SFSEG_RECORD, SFSEG_GENERIC = 1, 2, 4, 8
-SFSEG_FUSED, SFSEG_AUTOTUNE = 16, 32
-SFSEG_PATH_FAST, SFSEG_PATH_GENERIC, SFSEG_PATH_FUSED = 0, 1, 2
-PATH_NAMES = {SFSEG_PATH_FAST: "fast", SFSEG_PATH_GENERIC: "generic", SFSEG_PATH_FUSED: "fused"}
+SFSEG_FUSED, SFSEG_AUTOTUNE, SFSEG_CLUSTER = 16, 32, 64
+SFSEG_PATH_FAST, SFSEG_PATH_GENERIC, SFSEG_PATH_FUSED, SFSEG_PATH_CLUSTER = 0, 1, 2, 3
+PATH_NAMES = {SFSEG_PATH_FAST: "fast", SFSEG_PATH_GENERIC: "generic", SFSEG_PATH_FUSED: "fused",
+              SFSEG_PATH_CLUSTER: "cluster"}
 STORAGE = {"f32": SFSEG_F32, "bf16": SFSEG_BF16, "f16": SFSEG_F16}
 
 # Every entry point declared in include/sfseg.h.
@@ -282,7 +283,7 @@ def sfseg_plan_segments(dims, n_sms: int):
 
 def sfseg_get_path(ctx: int):
     """(path, fused CTA count, [us per step measured per path or -1]) of a context."""
-    path, ctas, us = _i32(), _i32(), (_dbl * 3)()
+    path, ctas, us = _i32(), _i32(), (_dbl * 4)()
     _check(load_library().sfseg_get_path(ctx, ctypes.byref(path), ctypes.byref(ctas), us), ctx)
     return path.value, ctas.value, list(us)
 
@@ -464,7 +465,8 @@ class SFSeg:
         return sfseg_launch_count(self.ctx)
 
     def path(self):
-        """{'path': 'fast'|'generic'|'fused', 'fused_ctas': n, 'tuned_us': {...}}."""
+        """{'path': 'fast'|'generic'|'fused'|'cluster', 'fused_ctas': n (CTAs of the fused or
+        cluster launch), 'tuned_us': {...}}."""
         pth, ctas, us = sfseg_get_path(self.ctx)
         return {"path": PATH_NAMES[pth], "fused_ctas": ctas,
                 "tuned_us": {PATH_NAMES[i]: u for i, u in enumerate(us) if u >= 0}}

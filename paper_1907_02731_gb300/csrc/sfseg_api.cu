@@ -88,7 +88,10 @@ struct sfseg_ctx {
     // all steps in one cooperative launch (step_fused.cu)
     int path = SFSEG_PATH_FAST;
     bool tune_pending = false;  // SFSEG_AUTOTUNE: choose the path at the first power_iterate
-    double tuned_us[3] = {-1.0, -1.0, -1.0};   // measured us per step of each path (-1: not timed)
+    double tuned_us[4] = {-1.0, -1.0, -1.0, -1.0};   // measured us per step of each path (-1: not timed)
+    // cluster path (step_cluster.cu): one small video resident in one cluster
+    bool cluster_ok = false;
+    ClusterPlan cplan{};
     // fused path: phase-2 runs, barrier words, scratch (allocated on first use)
     bool fused_ok = false;      // the context can run the fused kernel
     int fused_max = 0;          // co-resident CTAs of the fused kernel on this device
@@ -159,8 +162,14 @@ static sfseg_status validate(const sfseg_params* p) {
     if (p->storage < 0 || p->storage > 2)
         return fail(nullptr, SFSEG_EINVAL, "storage %d is not an sfseg_dtype", p->storage);
     if (p->flags & ~(SFSEG_S_IS_SP | SFSEG_NO_GRAPH | SFSEG_RECORD | SFSEG_GENERIC | SFSEG_FUSED |
-                     SFSEG_AUTOTUNE))
+                     SFSEG_AUTOTUNE | SFSEG_CLUSTER))
         return fail(nullptr, SFSEG_EINVAL, "flags 0x%x: unknown bits", (unsigned)p->flags);
+    if ((p->flags & SFSEG_CLUSTER) && (p->flags & (SFSEG_GENERIC | SFSEG_FUSED | SFSEG_AUTOTUNE)))
+        return fail(nullptr, SFSEG_EINVAL, "SFSEG_CLUSTER excludes SFSEG_GENERIC, SFSEG_FUSED and SFSEG_AUTOTUNE");
+    if ((p->flags & SFSEG_CLUSTER) && (p->flags & SFSEG_RECORD))
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "SFSEG_RECORD runs the per-step kernel (no SFSEG_CLUSTER)");
+    if ((p->flags & SFSEG_CLUSTER) && p->nchan != 1)
+        return fail(nullptr, SFSEG_EUNSUPPORTED, "the cluster kernel runs one channel (nchan = 1)");
     if ((p->flags & SFSEG_FUSED) && (p->flags & (SFSEG_GENERIC | SFSEG_AUTOTUNE)))
         return fail(nullptr, SFSEG_EINVAL, "SFSEG_FUSED excludes SFSEG_GENERIC and SFSEG_AUTOTUNE");
     if ((p->flags & (SFSEG_FUSED | SFSEG_AUTOTUNE)) && (p->flags & SFSEG_RECORD))
@@ -599,7 +608,20 @@ static sfseg_status create_impl(const sfseg_params* prm, int nv, const int32_t* 
             if (e == cudaSuccess) c->fused_ok = true;
         }
     }
+    if (e == cudaSuccess && nv == 1 && prm->nchan == 1 && !(prm->flags & SFSEG_RECORD) && f_lo == 0 && f_hi < 0)
+        c->cluster_ok = plan_step_cluster(prm->storage, prm->rt, prm->ry, prm->rx, c->geo[0].nf, c->geo[0].h,
+                                          c->geo[0].w, &c->cplan);
     c->path = c->fast ? SFSEG_PATH_FAST : SFSEG_PATH_GENERIC;
+    if (e == cudaSuccess && (prm->flags & SFSEG_CLUSTER)) {
+        if (!c->cluster_ok) {
+            fail(nullptr, SFSEG_EUNSUPPORTED,
+                 "SFSEG_CLUSTER: needs one video, radii (3,3,3), (2,5,5) or (2,4,4), at most 16 tiles of 16 "
+                 "columns whose frames fit one CTA's shared memory, and a device that schedules the cluster");
+            free_ctx(c);
+            return SFSEG_EUNSUPPORTED;
+        }
+        c->path = SFSEG_PATH_CLUSTER;
+    }
     if (e == cudaSuccess && (prm->flags & SFSEG_FUSED)) {
         if (!c->fused_ok) {
             fail(nullptr, SFSEG_EUNSUPPORTED, "SFSEG_FUSED: this device has no cooperative launch");
@@ -774,6 +796,23 @@ static sfseg_status run_fused(sfseg_ctx* c, int n, bool final_mode, cudaStream_t
     F.bar = c->d_fbar;
     CUDA_OR(c, cudaMemsetAsync(c->d_fbar, 0, sizeof(unsigned) * 3, s));
     CUDA_OR(c, launch_step_fused(c->prm.storage, F, c->fused_ctas, s));
+    c->launches += 1;
+    return SFSEG_OK;
+}
+
+// All n power steps of a call in one cluster launch (step_cluster.cu); the
+// last step writes the caller's FP32 buffer when final_mode is set.
+static sfseg_status run_cluster(sfseg_ctx* c, int n, bool final_mode, cudaStream_t s) {
+    if (n <= 0) return SFSEG_OK;
+    ClusterParams C{};
+    C.S = step_params(c, 0, final_mode, true);
+    C.buf0 = c->xa;
+    C.buf1 = c->xb;
+    C.n_steps = n;
+    C.final_mode = final_mode ? 1 : 0;
+    C.tiles_x = c->cplan.tiles_x;
+    C.th = c->cplan.th;
+    CUDA_OR(c, launch_step_cluster(c->prm.storage, C, c->cplan, s));
     c->launches += 1;
     return SFSEG_OK;
 }
@@ -958,7 +997,7 @@ static sfseg_status iterate_record(sfseg_ctx* c, const float* d_x_in, float* d_x
 static constexpr long long kFusedTuneMaxVoxels = 8ll << 20;   // scratch 3 x 4 B x N <= 96 MiB
 static constexpr int kTuneSteps = 6;
 
-struct TuneChoice { int path, ctas; double us[3]; };
+struct TuneChoice { int path, ctas; double us[4]; };
 static std::mutex g_tune_mu;
 static std::map<std::string, TuneChoice> g_tune_cache;
 
@@ -1000,6 +1039,7 @@ static sfseg_status autotune(sfseg_ctx* c, const float* const* d_x_in, cudaStrea
     std::vector<Cand> cands;
     if (c->fast) cands.push_back({SFSEG_PATH_FAST, 0});
     cands.push_back({SFSEG_PATH_GENERIC, 0});
+    if (c->cluster_ok) cands.push_back({SFSEG_PATH_CLUSTER, 0});
     if (c->fused_ok && c->total <= kFusedTuneMaxVoxels) {
         const int g0 = fused_default_ctas(c);
         for (int g : {g0, (g0 + 1) / 2, (g0 + 3) / 4})
@@ -1011,7 +1051,7 @@ static sfseg_status autotune(sfseg_ctx* c, const float* const* d_x_in, cudaStrea
     CUDA_OR(c, cudaEventCreate(&e1));
     double best = 1e300;
     Cand pick = cands[0];
-    double us_path[3] = {-1.0, -1.0, -1.0};
+    double us_path[4] = {-1.0, -1.0, -1.0, -1.0};
     sfseg_status st = SFSEG_OK;
     for (const Cand& cd : cands) {
         if ((st = set_path(c, cd.path, cd.ctas)) != SFSEG_OK) break;
@@ -1020,7 +1060,9 @@ static sfseg_status autotune(sfseg_ctx* c, const float* const* d_x_in, cudaStrea
             cudaEventRecord(e0, s);
             for (int v = 0; v < c->nv && st == SFSEG_OK; ++v) st = prep_x(c, v, d_x_in[v], false, 0.0, s);
             if (st != SFSEG_OK) break;
-            st = cd.path == SFSEG_PATH_FUSED ? run_fused(c, kTuneSteps, false, s) : run_steps(c, kTuneSteps, s);
+            st = cd.path == SFSEG_PATH_FUSED     ? run_fused(c, kTuneSteps, false, s)
+                 : cd.path == SFSEG_PATH_CLUSTER ? run_cluster(c, kTuneSteps, false, s)
+                                                 : run_steps(c, kTuneSteps, s);
             if (st != SFSEG_OK) break;
             cudaEventRecord(e1, s);
             cudaError_t e = cudaEventSynchronize(e1);
@@ -1047,7 +1089,7 @@ static sfseg_status autotune(sfseg_ctx* c, const float* const* d_x_in, cudaStrea
     if (st != SFSEG_OK) return st;
     drop_graphs(c);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    TuneChoice tc{pick.path, pick.ctas, {us_path[0], us_path[1], us_path[2]}};
+    TuneChoice tc{pick.path, pick.ctas, {us_path[0], us_path[1], us_path[2], us_path[3]}};
     g_tune_cache[key] = tc;
     return SFSEG_OK;
 }
@@ -1083,12 +1125,12 @@ static sfseg_status iterate_impl(sfseg_ctx* c, const float* const* d_x_in, float
         if (st != SFSEG_OK) return st;
     }
     const bool final_mode = (K > 0 && tol == 0.0);
-    if (c->path == SFSEG_PATH_FUSED) {
+    if (c->path == SFSEG_PATH_FUSED || c->path == SFSEG_PATH_CLUSTER) {
         if (final_mode) {
             CUDA_OR(c, launch_set_ptrs(c->d_out, d_x, c->nv, s));
             c->launches += 1;
         }
-        st = run_fused(c, K, final_mode, s);
+        st = c->path == SFSEG_PATH_FUSED ? run_fused(c, K, final_mode, s) : run_cluster(c, K, final_mode, s);
         if (st != SFSEG_OK) return st;
     } else {
         st = run_steps(c, final_mode ? K - 1 : K, s);
@@ -1126,6 +1168,7 @@ namespace sfseg {
 void sfseg_debug_take_fast(unsigned long long* out);
 void sfseg_debug_take_generic(unsigned long long* out);
 void sfseg_debug_take_fused(unsigned long long* out);
+void sfseg_debug_take_cluster(unsigned long long* out);
 }  // namespace sfseg
 
 // ======================================================================= C-ABI
@@ -1144,7 +1187,7 @@ sfseg_status sfseg_debug_status(int64_t* count, int32_t* code, int64_t* a, int64
     if (e != cudaSuccess) return fail(nullptr, SFSEG_ECUDA, "debug status: %s", cudaGetErrorString(e));
     unsigned long long n = 0, first[3] = {0, 0, 0};
     void (*take[])(unsigned long long*) = {sfseg_debug_take_fast, sfseg_debug_take_generic,
-                                           sfseg_debug_take_fused};
+                                           sfseg_debug_take_fused, sfseg_debug_take_cluster};
     for (auto fn : take) {
         unsigned long long w[4];
         fn(w);
@@ -1627,6 +1670,8 @@ sfseg_status sfseg_get_warnings(sfseg_ctx* c, int32_t* flags) {
 sfseg_status sfseg_debug_inject_timeout(sfseg_ctx* c, int32_t n_steps) {
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (n_steps < 0) return fail(c, SFSEG_EINVAL, "n_steps must be >= 0");
+    if (c->path == SFSEG_PATH_CLUSTER)
+        return fail(c, SFSEG_EUNSUPPORTED, "the cluster launch has no timed wait to inject into");
     if (!c->fast && c->path != SFSEG_PATH_FUSED)
         return fail(c, SFSEG_EUNSUPPORTED,
                     "timeouts exist only in the specialised step kernel and the fused launch");
@@ -1667,8 +1712,9 @@ sfseg_status sfseg_create_slab(const sfseg_params* prm, int32_t own_lo, int32_t 
     if (out) *out = nullptr;
     sfseg_status st = validate(prm);
     if (st != SFSEG_OK) return st;
-    if (prm->flags & (SFSEG_FUSED | SFSEG_AUTOTUNE | SFSEG_RECORD))
-        return fail(nullptr, SFSEG_EUNSUPPORTED, "a slab runs the per-step kernels (no FUSED, AUTOTUNE, RECORD)");
+    if (prm->flags & (SFSEG_FUSED | SFSEG_AUTOTUNE | SFSEG_RECORD | SFSEG_CLUSTER))
+        return fail(nullptr, SFSEG_EUNSUPPORTED,
+                    "a slab runs the per-step kernels (no FUSED, AUTOTUNE, RECORD, CLUSTER)");
     if (own_lo < 0 || own_hi > prm->nf || own_lo >= own_hi)
         return fail(nullptr, SFSEG_EINVAL, "own frames [%d, %d) outside the slab's %d frames", own_lo, own_hi,
                     prm->nf);
@@ -1815,7 +1861,9 @@ sfseg_status sfseg_slab_output(sfseg_ctx* c, float* d_x, void* stream) {
 sfseg_status sfseg_get_path(const sfseg_ctx* c, int32_t* path, int32_t* fused_ctas, double* us_per_step) {
     if (!c) return fail(nullptr, SFSEG_EINVAL, "ctx is NULL");
     if (path) *path = c->path;
-    if (fused_ctas) *fused_ctas = c->path == SFSEG_PATH_FUSED ? c->fused_ctas : 0;
+    if (fused_ctas)
+        *fused_ctas = c->path == SFSEG_PATH_FUSED ? c->fused_ctas
+                      : c->path == SFSEG_PATH_CLUSTER ? c->cplan.n_ctas : 0;
     if (us_per_step) memcpy(us_per_step, c->tuned_us, sizeof c->tuned_us);
     return SFSEG_OK;
 }

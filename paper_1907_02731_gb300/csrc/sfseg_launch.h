@@ -196,6 +196,25 @@ __host__ __device__ inline int fused_rows2(int w) {
     return r < 1 ? 1 : r;
 }
 
+// ------------------------------------------------------------- cluster
+// All K steps of one small video in one thread-block cluster (step_cluster.cu).
+struct ClusterParams {
+    StepParams S;               // taps, alpha, geo, sp, f, state, trace, final_out (video 0)
+    const void* buf0;           // stored x0 (x_a); the result goes to buf0 / buf1 by iter parity
+    void* buf1;                 // x_b
+    int n_steps;                // K
+    int final_mode;             // the last step writes the caller's FP32 buffer (S.final_out[0])
+    int tiles_x;                // tile columns of the cluster (CTA rank = ty * tiles_x + tx)
+    int th;                     // tile height (a multiple of 8); tiles are 16 columns wide
+};
+struct ClusterPlan {
+    int n_ctas;                 // CTAs of the one cluster (at most 16)
+    int tiles_x, th;
+    size_t smem;                // dynamic shared memory per CTA
+};
+bool plan_step_cluster(int storage, int rt, int ry, int rx, int nf, int h, int w, ClusterPlan* out);
+cudaError_t launch_step_cluster(int storage, const ClusterParams& C, const ClusterPlan& plan, cudaStream_t s);
+
 size_t fused_smem_bytes(int ry, int rx);
 void fused_tile(int* tx, int* ty, int* threads);
 cudaError_t setup_step_fused(int storage, int ry, int rx, int* max_ctas);

@@ -46,8 +46,9 @@ def test_default_params_and_status_strings(lib):
 
 @pytest.mark.parametrize("field,value", [("rx", -1), ("ry", 17), ("rt", 9), ("sigma_t", 0.0),
                                          ("alpha", -1.0), ("p", float("nan")), ("storage", 3),
-                                         ("nf", 0), ("w", -5), ("nchan", 0), ("flags", 64),
-                                         ("flags", -1), ("flags", 16 | 8), ("flags", 16 | 32)])
+                                         ("nf", 0), ("w", -5), ("nchan", 0), ("flags", 128),
+                                         ("flags", -1), ("flags", 16 | 8), ("flags", 16 | 32),
+                                         ("flags", 64 | 8), ("flags", 64 | 16), ("flags", 64 | 32)])
 def test_create_rejects_bad_params(lib, field, value):
     """Validation happens on the host before any device call."""
     p = sf.sfseg_default_params(4, 8, 8)
@@ -58,10 +59,11 @@ def test_create_rejects_bad_params(lib, field, value):
     assert sf.sfseg_last_error(None)
 
 
-@pytest.mark.parametrize("flags,nchan", [(16 | 4, 1), (32 | 4, 1), (16, 2)])
+@pytest.mark.parametrize("flags,nchan", [(16 | 4, 1), (32 | 4, 1), (16, 2), (64 | 4, 1), (64, 2)])
 def test_create_rejects_unsupported_paths(lib, flags, nchan):
-    """The fused launch runs one channel and is not recorded for the adjoint;
-    the autotuner does not choose for recorded contexts (host-side checks)."""
+    """The fused and cluster launches run one channel and are not recorded for
+    the adjoint; the autotuner does not choose for recorded contexts (host-side
+    checks)."""
     p = sf.sfseg_default_params(4, 8, 8)
     p.flags, p.nchan = flags, nchan
     with pytest.raises(sf.SFSegError) as ei:
@@ -119,7 +121,7 @@ def test_slab_arguments_are_checked(lib):
     with pytest.raises(sf.SFSegError) as ei:
         sf.sfseg_create_slab(p, 2, 6, 10)                       # fewer video voxels than its own frames
     assert ei.value.status == sf.SFSEG_EINVAL
-    for flags in (sf.SFSEG_FUSED, sf.SFSEG_AUTOTUNE, sf.SFSEG_RECORD):
+    for flags in (sf.SFSEG_FUSED, sf.SFSEG_AUTOTUNE, sf.SFSEG_RECORD, sf.SFSEG_CLUSTER):
         p.flags = flags
         with pytest.raises(sf.SFSegError) as ei:
             sf.sfseg_create_slab(p, 2, 6, 8 * 16 * 16 * 4)

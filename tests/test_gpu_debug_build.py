@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_gpu_parity.py", "tests/test_gpu_fused.py", "tests/test_gpu_slab.py",
-          "tests/test_gpu_multichannel.py"]
+          "tests/test_gpu_multichannel.py", "tests/test_gpu_cluster.py"]
 
 
 def test_parity_suites_under_the_bounds_checked_build(cuda_device):

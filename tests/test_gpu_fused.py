@@ -158,8 +158,9 @@ def test_fused_barrier_timeout_is_reported_and_recovers(cuda_device):
 
 
 def test_autotune_choice_matches_oracle_and_is_cached(cuda_device):
-    """The autotuner times the per-step kernels and the fused launch on the
-    context's own inputs; whichever it keeps, the result is the oracle's."""
+    """The autotuner times the per-step kernel, the fused launch and the
+    cluster launch on the context's own inputs; whichever it keeps, the result
+    is the oracle's."""
     import torch
     wl = inputs.WORKLOADS["small_16x64x64"]
     radii, sig = (wl.rt, wl.ry, wl.rx), (wl.sigma_t, wl.sigma_xy, wl.sigma_xy)
@@ -170,8 +171,8 @@ def test_autotune_choice_matches_oracle_and_is_cached(cuda_device):
         x = eng.power_iterate(d, d, d.clone(), wl.iters)
         torch.cuda.synchronize()
         info = eng.path()
-        assert info["path"] in ("generic", "fused")        # 7x7x7 has no specialised kernel
-        assert set(info["tuned_us"]) == {"generic", "fused"}
+        assert info["path"] in ("generic", "fused", "cluster")   # 7x7x7 has no specialised kernel
+        assert set(info["tuned_us"]) == {"generic", "fused", "cluster"}
         assert all(u > 0 for u in info["tuned_us"].values())
         best = min(info["tuned_us"], key=info["tuned_us"].get)
         assert info["path"] == best
@@ -213,7 +214,7 @@ def test_autotune_batched_matches_oracle(cuda_device):
 
 
 def test_autotuned_context_serves_every_entry_point(cuda_device):
-    """After the autotuner kept the fused launch, the per-step entry points of
+    """After the autotuner kept the fused or cluster launch, the per-step entry points of
     the same context (Rayleigh quotient, one application of M, the binarised
     iteration) still run their one-launch-per-step kernels and match the
     oracle."""
@@ -227,7 +228,7 @@ def test_autotuned_context_serves_every_entry_point(cuda_device):
         d = to_dev(f)
         x = eng.power_iterate(d, d, d.clone(), 10)
         torch.cuda.synchronize()
-        assert eng.path()["path"] in ("fast", "fused")
+        assert eng.path()["path"] in ("fast", "fused", "cluster")
         ref = oracle_power(f, f, 10, radii, sig, 1.0, 0.1)
         assert rel_l2(x.cpu().numpy(), ref["x"]) < TOL_F32
         xv = rng.standard_normal(shape).astype(np.float32)
