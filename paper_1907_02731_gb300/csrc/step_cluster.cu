@@ -64,23 +64,36 @@ struct Cfg {
     // in 8 distinct bank groups)
     static constexpr int YW0 = TW - 4 + 4 * NQ;
     static constexpr int YW = ((YW0 / 4) & 1) ? YW0 : YW0 + 4;
-    static constexpr int PW = TW + 4;                      // row stride of the channel planes (5 chunks)
+    static constexpr int PW = TW + 4;                      // row stride of the C2 planes (5 chunks)
+    // channels C0 and C1 travel as interleaved pairs (packed FMAs): the
+    // x-pass window of 4 outputs is NQ2 16-byte loads of two column pairs; row
+    // strides in pairs, an odd number of 16-byte chunks
+    static constexpr int NQ2 = (4 + 2 * RX + 1) / 2;
+    static constexpr int YW20 = (EW > TW - 4 + 2 * NQ2 ? EW : TW - 4 + 2 * NQ2);
+    static constexpr int YW2 = (((YW20 + 1) / 2) & 1) ? (YW20 + 1) / 2 * 2 : (YW20 + 1) / 2 * 2 + 2;
+    static constexpr int PW2 = TW + 2;
     static constexpr int NR = 2 * RT + 1;
     static_assert(EW <= 32, "the extended tile row must fit the lanes of a warp");
     static_assert(YW >= EW, "y-pass rows hold the extended columns");
+    static_assert(((YW2 / 2) & 1) && ((PW2 / 2) & 1) && YW2 >= EW, "pair strides");
 };
 
 // Shared-memory layout (floats) for nf frames and tile height th.
 struct Layout {
-    int eh, ew, yw, pw;
-    long long spe, fe, xe, zt0, zt1, pv, yrow, total;
+    int eh, ew, yw, pw, yw2, pw2;
+    long long spe, fe, xe, zt0, zt1, pv01, pv2, yrow, total;
 };
-__host__ __device__ inline Layout layout(int nf, int th, int ry, int rx, int yw, int pw) {
+struct Strides {
+    int yw, pw, yw2, pw2;
+};
+__host__ __device__ inline Layout layout(int nf, int th, int ry, int rx, Strides S) {
     Layout L;
     L.eh = th + 2 * ry;
     L.ew = TW + 2 * rx;
-    L.yw = yw;
-    L.pw = pw;
+    L.yw = S.yw;
+    L.pw = S.pw;
+    L.yw2 = S.yw2;
+    L.pw2 = S.pw2;
     // every array starts on a 16-byte boundary (float4 access)
     const long long ext = ((long long)nf * L.eh * L.ew + 3) & ~3ll;
     const long long tile = (long long)nf * th * TW;
@@ -89,15 +102,16 @@ __host__ __device__ inline Layout layout(int nf, int th, int ry, int rx, int yw,
     L.xe = L.fe + ext;
     L.zt0 = L.xe + ext;
     L.zt1 = L.zt0 + tile;
-    L.pv = L.zt1 + tile;                                   // [3][nf][th][pw]
-    L.yrow = L.pv + 3ll * nf * th * pw;                    // [NWARP][3][RC][yw]
-    L.total = L.yrow + (long long)NWARP * 3 * RC * yw;
+    L.pv01 = L.zt1 + tile;                                 // [nf][th][pw2] (C0, C1) pairs
+    L.pv2 = L.pv01 + 2ll * nf * th * L.pw2;                // [nf][th][pw] C2
+    L.yrow = L.pv2 + (long long)nf * th * L.pw;            // per warp: [RC][yw2] pairs, [RC][yw]
+    L.total = L.yrow + (long long)NWARP * RC * (2 * L.yw2 + L.yw);
     L.total = (L.total + 3) & ~3ll;
     return L;
 }
 // bytes: the float arrays and the two record slots [2][kRed] (doubles)
-inline size_t smem_bytes(int nf, int th, int ry, int rx, int yw, int pw) {
-    const Layout L = layout(nf, th, ry, rx, yw, pw);
+inline size_t smem_bytes(int nf, int th, int ry, int rx, Strides S) {
+    const Layout L = layout(nf, th, ry, rx, S);
     return sizeof(float) * (size_t)L.total + sizeof(double) * 2 * kRed;
 }
 
@@ -127,11 +141,12 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
     extern __shared__ __align__(16) float sm[];
     const VideoGeom g = P.geo[0];
     const int nf = g.nf, th = C.th;
-    const Layout L = layout(nf, th, RY, RX, Q::YW, Q::PW);
+    const Layout L = layout(nf, th, RY, RX, Strides{Q::YW, Q::PW, Q::YW2, Q::PW2});
     float* spe = sm + L.spe;
     float* fe = sm + L.fe;
     float* xe = sm + L.xe;
-    float* pv = sm + L.pv;
+    float2* pv01 = reinterpret_cast<float2*>(sm + L.pv01);
+    float* pv2 = sm + L.pv2;
     double* slots = reinterpret_cast<double*>(sm + L.total);   // [2][kRed]
     __shared__ VState s_st;
     __shared__ float s_scale, s_sg, s_shift;
@@ -296,7 +311,8 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
         // tasks (frame, 8-row chunk) from a shared counter: warp 0 takes its
         // share once its update is done
         {
-            float* yr = sm + L.yrow + (long long)warp * 3 * RC * Q::YW;
+            float2* yr01 = reinterpret_cast<float2*>(sm + L.yrow + (long long)warp * RC * (2 * Q::YW2 + Q::YW));
+            float* yr2 = reinterpret_cast<float*>(yr01 + RC * Q::YW2);
             const int nchunk = th / RC, ntask = nf * nchunk;
             for (;;) {
                 int task = 0;
@@ -306,37 +322,59 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
                 const int t = task / nchunk, c = task - t * nchunk;
                 if (lane < EW) {
                     const int b = (t * eh + c * RC) * EW + lane;
-                    float acc[RC][3];
+                    float2 acc01[RC];
+                    float acc2[RC];
 #pragma unroll
                     for (int i = 0; i < RC + 2 * RY; ++i) {
                         const float a0 = spe[b + i * EW] * xe[b + i * EW];
                         const float fv = fe[b + i * EW];
                         const float a1 = fv * a0, a2 = fv * a1;
+                        const float2 a01 = make_float2(a0, a1);
 #pragma unroll
                         for (int j = 0; j < RC; ++j) {
                             const int d = i - j;
                             if (d == 0) {
-                                acc[j][0] = P.gy[0] * a0;
-                                acc[j][1] = P.gy[0] * a1;
-                                acc[j][2] = P.gy[0] * a2;
+                                acc01[j] = __fmul2_rn(a01, P.gy2[0]);
+                                acc2[j] = P.gy[0] * a2;
                             } else if (d > 0 && d <= 2 * RY) {
-                                acc[j][0] = fmaf(P.gy[d], a0, acc[j][0]);
-                                acc[j][1] = fmaf(P.gy[d], a1, acc[j][1]);
-                                acc[j][2] = fmaf(P.gy[d], a2, acc[j][2]);
+                                acc01[j] = __ffma2_rn(a01, P.gy2[d], acc01[j]);
+                                acc2[j] = fmaf(P.gy[d], a2, acc2[j]);
                             }
                         }
                     }
 #pragma unroll
-                    for (int j = 0; j < RC; ++j)
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) yr[(ch * RC + j) * Q::YW + lane] = acc[j][ch];
+                    for (int j = 0; j < RC; ++j) {
+                        yr01[j * Q::YW2 + lane] = acc01[j];
+                        yr2[j * Q::YW + lane] = acc2[j];
+                    }
                 }
                 __syncwarp();
                 {
                     const int gi = lane >> 3, j = lane & 7;   // 4-column group, row of the task
+                    // (C0, -2 C1) with the pair taps (g, -2 g): the factor is exact
+                    {
+                        const float2* row = yr01 + j * Q::YW2 + 4 * gi;
+                        float2 w[2 * Q::NQ2];
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        const float* row = yr + (ch * RC + j) * Q::YW + 4 * gi;
+                        for (int q = 0; q < Q::NQ2; ++q) {
+                            const float4 v = *reinterpret_cast<const float4*>(row + 2 * q);
+                            w[2 * q] = make_float2(v.x, v.y);
+                            w[2 * q + 1] = make_float2(v.z, v.w);
+                        }
+                        float2 o[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float2 a = __fmul2_rn(w[i], P.gx2[0]);
+#pragma unroll
+                            for (int d = 1; d <= 2 * RX; ++d) a = __ffma2_rn(w[i + d], P.gx2[d], a);
+                            o[i] = a;
+                        }
+                        float4* dst = reinterpret_cast<float4*>(pv01 + (t * th + c * RC + j) * Q::PW2 + 4 * gi);
+                        dst[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                        dst[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+                    }
+                    {
+                        const float* row = yr2 + j * Q::YW + 4 * gi;
                         float w[4 * Q::NQ];
 #pragma unroll
                         for (int q = 0; q < Q::NQ; ++q) {
@@ -351,7 +389,7 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
                             for (int d = 1; d <= 2 * RX; ++d) a = fmaf(P.gx[d], w[i + d], a);
                             o[i] = a;
                         }
-                        float* dst = pv + ((ch * nf + t) * th + c * RC + j) * Q::PW + 4 * gi;
+                        float* dst = pv2 + (t * th + c * RC + j) * Q::PW + 4 * gi;
                         *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
                     }
                 }
@@ -372,27 +410,33 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
             const int fg_n = NTH / ncol > 0 ? (NTH / ncol < nf ? NTH / ncol : nf) : 1;
             float part[kRed] = {0.f, 0.f, 0.f, 0.f};
             float* FO = final_step ? P.final_out[0] : nullptr;
-            const int plane_pv = th * Q::PW;
+            const int plane01 = th * Q::PW2, plane2 = th * Q::PW;
             for (int idx = tid; idx < ncol * fg_n; idx += NTH) {
                 const int fgi = idx / ncol, col = idx - fgi * ncol;
                 const int ly = col / TW, lx = col - ly * TW;
                 const int yy = y0 + ly, xx = x0 + lx;
                 const bool in_vid = yy < g.h && xx < g.w;
                 const int ta = fgi * nf / fg_n, tb = (fgi + 1) * nf / fg_n;
-                const float* pc = pv + ly * Q::PW + lx;          // + (ch nf + t) plane_pv
+                const float2* pc01 = pv01 + ly * Q::PW2 + lx;    // + t plane01
+                const float* pc2 = pv2 + ly * Q::PW + lx;        // + t plane2
                 const int e0 = (ly + RY) * EW + lx + RX;         // + t eh EW
-                float ring[NR][3];
+                float2 ring01[NR];
+                float ring2[NR];
 #pragma unroll
-                for (int s = 0; s < NR; ++s) ring[s][0] = ring[s][1] = ring[s][2] = 0.f;
+                for (int s = 0; s < NR; ++s) {
+                    ring01[s] = make_float2(0.f, 0.f);
+                    ring2[s] = 0.f;
+                }
                 int tin = ta - RT;
                 const int t_end = tb + RT;
                 auto frame = [&](auto phase) -> bool {
                     constexpr int U = decltype(phase)::value;
                     if (tin >= t_end) return false;
-                    float p[3] = {0.f, 0.f, 0.f};
+                    float2 p01 = make_float2(0.f, 0.f);
+                    float p2 = 0.f;
                     if (tin >= 0 && tin < nf) {
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) p[ch] = pc[(ch * nf + tin) * plane_pv];
+                        p01 = pc01[tin * plane01];
+                        p2 = pc2[tin * plane2];
                     }
                     // input frame tin is tap d = 2 RT - m of output tin - RT + m
                     // (the first of its taps when m = 2 RT); slot (U - RT + m)
@@ -400,22 +444,24 @@ __global__ void __launch_bounds__(NTH, 1) step_cluster_kernel(const __grid_const
 #pragma unroll
                     for (int m = 0; m < NR; ++m) {
                         const int slot = ((U - RT + m) % NR + NR) % NR;
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            if (m == NR - 1) ring[slot][ch] = P.gt[NR - 1 - m] * p[ch];
-                            else ring[slot][ch] = fmaf(P.gt[NR - 1 - m], p[ch], ring[slot][ch]);
+                        if (m == NR - 1) {
+                            ring01[slot] = __fmul2_rn(p01, P.gt2[NR - 1 - m]);
+                            ring2[slot] = P.gt[NR - 1 - m] * p2;
+                        } else {
+                            ring01[slot] = __ffma2_rn(p01, P.gt2[NR - 1 - m], ring01[slot]);
+                            ring2[slot] = fmaf(P.gt[NR - 1 - m], p2, ring2[slot]);
                         }
                     }
                     constexpr int s0 = ((U - RT) % NR + NR) % NR;   // output tin - RT is complete
                     const int o = tin - RT;
                     if (o >= ta && o < tb && in_vid) {
-                        const float c0 = ring[s0][0], c1 = ring[s0][1], c2 = ring[s0][2];
+                        const float c0 = ring01[s0].x, c1m2 = ring01[s0].y, c2 = ring2[s0];   // c1m2 = -2 C1
                         const int e = o * eh * EW + e0;
                         const float s = spe[e], fv = fe[e];
                         const int zo = o * th * TW + col;
                         const float xh = scale * zin[zo];
                         const float af = alpha * fv;
-                        const float inner = fmaf(-af, fv, 1.f) * c0 + 2.f * af * c1 - alpha * c2;
+                        const float inner = fmaf(-af, c1m2, fmaf(-af, fv, 1.f) * c0) - alpha * c2;
                         float z = sg * (s * inner);
                         if (FO) {
                             FO[((long long)o * g.h + yy) * g.w + xx] = z;
@@ -486,18 +532,18 @@ struct Inst {
         }
         return nullptr;
     }
-    static void strides(int* yw, int* pw) {
-        *yw = Cfg<RT, RY, RX>::YW;
-        *pw = Cfg<RT, RY, RX>::PW;
+    static clu::Strides strides() {
+        using Q = Cfg<RT, RY, RX>;
+        return clu::Strides{Q::YW, Q::PW, Q::YW2, Q::PW2};
     }
 };
 
 // the radii the cluster kernel is compiled for: (rt, ry, rx)
-static bool lookup(int rt, int ry, int rx, int storage, const void** fn, int* yw, int* pw) {
+static bool lookup(int rt, int ry, int rx, int storage, const void** fn, Strides* st) {
 #define SFSEG_CLU(A, B, D)                                        \
     if (rt == A && ry == B && rx == D) {                          \
         *fn = Inst<A, B, D>::fn(storage);                         \
-        Inst<A, B, D>::strides(yw, pw);                           \
+        *st = Inst<A, B, D>::strides();                           \
         return *fn != nullptr;                                    \
     }
     SFSEG_CLU(3, 3, 3)
@@ -518,8 +564,8 @@ SFSEG_DEBUG_TU(cluster)
 // schedulable).  Returns false when the video does not qualify.
 bool plan_step_cluster(int storage, int rt, int ry, int rx, int nf, int h, int w, ClusterPlan* out) {
     const void* fn = nullptr;
-    int yw = 0, pw = 0;
-    if (!clu::lookup(rt, ry, rx, storage, &fn, &yw, &pw)) return false;
+    clu::Strides st{};
+    if (!clu::lookup(rt, ry, rx, storage, &fn, &st)) return false;
     if (nf < 1 || h < 1 || w < 1) return false;
     int dev = 0, smem_optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -539,7 +585,7 @@ bool plan_step_cluster(int storage, int rt, int ry, int rx, int nf, int h, int w
         // the kernel's 32-bit reciprocal divisions need indices below 2^16
         const long long nh = 2ll * ry * (clu::TW + 2 * rx) + 2ll * th * rx;
         if ((long long)nf * nh + 8 * clu::NTH >= 65536 || (long long)nf * (th + 2 * ry) >= 65536) continue;
-        const size_t bytes = clu::smem_bytes(nf, th, ry, rx, yw, pw);
+        const size_t bytes = clu::smem_bytes(nf, th, ry, rx, st);
         if (bytes + 1024 > (size_t)smem_optin) continue;   // plus the static shared variables
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -576,8 +622,8 @@ bool plan_step_cluster(int storage, int rt, int ry, int rx, int nf, int h, int w
 
 cudaError_t launch_step_cluster(int storage, const ClusterParams& C, const ClusterPlan& plan, cudaStream_t s) {
     const void* fn = nullptr;
-    int yw = 0, pw = 0;
-    if (!clu::lookup(C.S.rt, C.S.ry, C.S.rx, storage, &fn, &yw, &pw)) return cudaErrorInvalidValue;
+    clu::Strides st{};
+    if (!clu::lookup(C.S.rt, C.S.ry, C.S.rx, storage, &fn, &st)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
