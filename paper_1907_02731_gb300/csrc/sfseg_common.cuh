@@ -261,12 +261,14 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Adds the warp's FP32 partials into lane 0's FP64 accumulators and clears them.
-__device__ __forceinline__ void warp_flush(float (&p)[kRed], double (&acc)[kRed]) {
+// Adds the warp's FP32 partials into lane 0's accumulators (FP64, or FP32
+// where a caller keeps only a few dozen flushes per accumulator) and clears them.
+template <typename A>
+__device__ __forceinline__ void warp_flush(float (&p)[kRed], A (&acc)[kRed]) {
 #pragma unroll
     for (int c = 0; c < kRed; ++c) {
         float s = warp_sum(p[c]);
-        if ((threadIdx.x & 31) == 0) acc[c] += (double)s;
+        if ((threadIdx.x & 31) == 0) acc[c] += (A)s;
         p[c] = 0.f;
     }
 }
