@@ -8,25 +8,30 @@
 // frames) keeps sp, f and the iterate in shared memory for the whole call of
 // Alg. 1 (Eq. 4 + Eq. 8), and per step:
 //
-//   halo     each CTA assembles the stored iterate over its tile plus the
-//            (RY, RX) halo for every frame, reading the neighbours' tiles
-//            through distributed shared memory (zero outside the video: the
-//            zero padding of Eq. 7's convolutions);
-//   y, x     per (frame, 8-row chunk) task, one warp: the point-wise products
-//            a0 = sp x, a1 = f a0, a2 = f a1 and the y-pass with the lanes on
-//            the extended columns and the rows unrolled (Eq. 7, Sec. 4), then
-//            the x-pass from a warp-private row buffer, into three FP32
-//            channel planes per frame;
+//   halo     warps 1..15 fetch the halo ring of each frame's extended tile
+//            (RY rows above and below, RX columns left and right) from the
+//            neighbouring CTAs' tile buffers through distributed shared memory
+//            (zero outside the video: the zero padding of Eq. 7's
+//            convolutions); the interior is the tile's own iterate, written by
+//            the previous step's combine;
+//   y, x     per (frame, 8-row chunk) task, one warp (tasks from a shared
+//            counter): the point-wise products a0 = sp x, a1 = f a0,
+//            a2 = f a1 and the y-pass with the lanes on the extended columns
+//            and the rows unrolled (Eq. 7, Sec. 4), then the x-pass from a
+//            warp-private row buffer; C0 and C1 travel as packed pairs;
 //   t, comb  per tile column and frame range, one thread: the temporal taps as
 //            a register ring, the combine y = sp [(1 - a f^2) C0 + 2 a f C1 -
 //            a C2] with the deferred scale and gain, the stored (rounded)
-//            iterate into the other of two tile buffers, the FP32/FP64 sums
-//            z.z, xh.z, xh.xh, |z - s xh|^2, one FP64 record per CTA;
-//   barrier  one cluster barrier; then every CTA sums the records of all CTAs
-//            in rank order and runs the same scalar update (finish_step of
-//            the other paths) on its own copy of the video's state, so all
-//            CTAs hold bitwise-identical scalars and take the same branch;
-//            rank 0 writes the trace row.
+//            iterate into the other of two tile buffers and into the extended
+//            tile's interior, the sums z.z, xh.z, xh.xh, |z - s xh|^2 in FP32
+//            trees over lanes and warps: one record per CTA;
+//   barrier  one cluster barrier; then warp 0 of every CTA fetches the 16
+//            records, sums them in a fixed FP64 tree and runs the scalar
+//            update (finish_step of the other paths) on the CTA's copy of the
+//            video's state -- while warps 1..15 already assemble the next halo
+//            and start the next y/x tasks, which need no scalar -- so all CTAs
+//            hold bitwise-identical scalars and take the same branch; rank 0
+//            writes the trace row.
 //
 // Waits: the only waits between CTAs are cluster barriers, which every CTA
 // reaches on the same control flow (its decisions come from the identical
