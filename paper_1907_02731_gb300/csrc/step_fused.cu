@@ -329,7 +329,10 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
                 float* FO = final_step ? P.final_out[v] : nullptr;
                 const float scale = s_scale, sg = s_sg, shift = s_shift;
                 float part[kRed] = {0.f, 0.f, 0.f, 0.f};
-                double acc[kRed] = {0.0, 0.0, 0.0, 0.0};
+                // the warp's running sums of its flushed partials (one per unit,
+                // a few per item) in FP32: FP64 adds on lane 0 cost ~0.3 us per
+                // step on this GPU's FP64 units; the block sum is FP64
+                float acc[kRed] = {0.f, 0.f, 0.f, 0.f};
                 for (int un = item.t0; un < item.t1; ++un) {
                     const int t = un / nchunk, r0 = (un - t * nchunk) * rows;
                     const int nr = min(rows, g.h - r0);
@@ -386,9 +389,11 @@ step_fused_kernel(const __grid_constant__ FusedParams F) {
                 }
                 // the run's FP64 sums go to its item slot (reduced after the barrier)
                 double* sh = reinterpret_cast<double*>(sm);
-                block_sum_lane0(acc, sh);
+                double run[kRed];
+                for (int c = 0; c < kRed; ++c) run[c] = (double)acc[c];
+                block_sum_lane0(run, sh);
                 if (threadIdx.x == 0)
-                    for (int c = 0; c < kRed; ++c) P.partials[(long long)it * kRed + c] = acc[c];
+                    for (int c = 0; c < kRed; ++c) P.partials[(long long)it * kRed + c] = run[c];
             }
         }
         if (!grid_barrier(F.bar, G, nb, false)) goto timed_out;
