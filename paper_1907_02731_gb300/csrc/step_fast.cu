@@ -387,10 +387,11 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
     // partials (one per 16 frames, a few dozen per run) into a running sum:
     // FP32 with FP32 storage -- FP64 adds sit on the warp's critical chain and
     // FP64 is slow on this GPU (measured at 854x480x72: 194.7 -> 188.2 us per
-    // step, iterates within 1e-7) -- and FP64 with 2-byte storage, where the
-    // FP32 form measured slower; the block and everything above sum in FP64.
+    // step, iterates within 1e-7) -- and FP64 with 2-byte storage and in the
+    // variant that stores the adjoint terms, where the FP32 form measured
+    // slower; the block and everything above sum in FP64.
     const int seg_b = P.cta_begin[blockIdx.x], seg_e = P.cta_begin[blockIdx.x + 1];
-    using WAcc = typename std::conditional<std::is_same<TS, float>::value, float, double>::type;
+    using WAcc = typename std::conditional<std::is_same<TS, float>::value && !AUX, float, double>::type;
     WAcc acc[kRed] = {0, 0, 0, 0};
     int run_v = -1, run_first = seg_b;
     for (int sg = seg_b; sg < seg_e; ++sg) {
