@@ -142,3 +142,21 @@ def test_debug_build_exports_the_same_entry_points():
     L.sfseg_debug_build.restype = ctypes.c_int32
     assert L.sfseg_debug_build() == 1
     assert sf.load_library().sfseg_debug_build() == (1 if os.environ.get("SFSEG_LIBRARY") == "debug" else 0)
+
+
+def test_binding_constants_match_the_header():
+    """The flag bits, step paths and status codes the binding uses are the
+    values include/sfseg.h declares (parsed from the header's enums)."""
+    txt = open(os.path.join(ROOT, "include", "sfseg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    declared = {k: int(v) for k, v in re.findall(r"\b(SFSEG_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    checked = 0
+    for name, value in declared.items():
+        if hasattr(sf, name):
+            assert getattr(sf, name) == value, name
+            checked += 1
+    for name in ("SFSEG_FUSED", "SFSEG_AUTOTUNE", "SFSEG_CLUSTER", "SFSEG_PATH_FAST", "SFSEG_PATH_GENERIC",
+                 "SFSEG_PATH_FUSED", "SFSEG_PATH_CLUSTER", "SFSEG_EUNSUPPORTED", "SFSEG_ETIMEOUT"):
+        assert name in declared and hasattr(sf, name), name
+    assert checked >= 15
+    assert set(sf.PATH_NAMES) == {v for k, v in declared.items() if k.startswith("SFSEG_PATH_")}
