@@ -32,9 +32,13 @@
 //           slot roles are fixed registers;
 //   combine y = sp [(1 - a f^2) C0 + 2 a f C1 - a C2] for frame t - RT, with
 //           the deferred scale and gain; 16-byte stores; FP32 partial sums of
-//           z.z, x.z, x.x, |z - s x|^2 per thread over at most 16 frames, FP64
-//           per warp; EMPTY mbarrier back to the y-pass warps.
-// Consecutive segments of one video on a CTA form a run with one FP64
+//           z.z, x.z, x.x, |z - s x|^2 per thread over at most 16 frames
+//           (packed over voxel pairs with FP32 storage), flushed into a
+//           running sum per warp (FP32 with FP32 storage, else FP64); EMPTY
+//           mbarrier back to the y-pass warps.
+// With 2-byte storage the y-pass takes sp x as a mixed-precision FMA of the
+// 2-byte operands (exact in FP32).
+// Consecutive segments of one video on a CTA form a run with one FP64 block
 // reduction and one arrival; the last CTA of each video to arrive reduces the
 // partials and updates the video's scalars (no CTA waits on another).
 // Variants (template flags): AUX also stores the per-voxel terms the adjoint
