@@ -43,8 +43,8 @@ STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
 # figure is reported as null.
 KERNEL_SOURCES = ("paper_1907_02731_gb300/csrc/step_fast.cu", "paper_1907_02731_gb300/csrc/sfseg_common.cuh")
 DRAM_TRAFFIC_PER_LAUNCH = {
-    ("video_72x480x854", "f32"): (367743744.0 + 98644736.0, "9c5bdf6a6ee82557"),
-    ("video_72x480x854", "bf16"): (181751296.0 + 39703296.0, "9c5bdf6a6ee82557"),
+    ("video_72x480x854", "f32"): (367743744.0 + 98644736.0, "f351d46bae071de7"),
+    ("video_72x480x854", "bf16"): (181751296.0 + 39703296.0, "f351d46bae071de7"),
 }
 
 

@@ -526,12 +526,13 @@ __global__ void __launch_bounds__(NT, 1) step_fast_kernel(const __grid_constant_
                     rc[k][i] = 0.f;
                 }
             float part[kRed] = {0.f, 0.f, 0.f, 0.f};
-            // FP32 storage: the four per-voxel sums run as packed FMAs over
-            // voxel pairs (x: voxels 0, 2; y: 1, 3), folded at each flush
-            // (measured 188.3 -> 186.4 us per step at 854x480x72; with 2-byte
-            // storage and in the adjoint-term variant the scalar form measured
-            // faster / spilled less)
-            constexpr bool kPairSums = std::is_same<TS, float>::value && !AUX;
+            // FP32 storage, 11x11x5: the four per-voxel sums run as packed FMAs
+            // over voxel pairs (x: voxels 0, 2; y: 1, 3), folded at each flush
+            // (measured 188.3 -> 186.4 us per step at 854x480x72); with 2-byte
+            // storage, at 9x9x5 (the 24-video batch: 114.3 -> 116.9 ms) and in
+            // the adjoint-term variant the scalar form measured faster or
+            // spilled less
+            constexpr bool kPairSums = std::is_same<TS, float>::value && !AUX && RX == 5;
             float2 pp[kRed];
 #pragma unroll
             for (int c = 0; c < kRed; ++c) pp[c] = make_float2(0.f, 0.f);
